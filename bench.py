@@ -1,0 +1,384 @@
+"""Throughput benchmark of the fused multicomponent TSLB step on GB300.
+
+Default workload: the axisymmetric jet on a 192 x 192 x 384 grid (nozzle
+D = 16 on the z = 0 face, u = 0.05, Re = 5000, We = 100, 1 % inlet noise,
+free-slip sides, outflow), FP32 storage.  One benchmark step is one lattice
+Boltzmann time step over the whole grid (one fused kernel launch).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tslb|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank advances its own
+replica of the workload on its own GPU (the method needs no exchange between
+independent jets); the value is the total lattice updates of all ranks over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS and % of HBM roofline on 1 GB300, FP32 vs FP16-storage vs batched"
+UNIT = "GLUPS"
+FIELDS = 11  # stored values per node: rho - 1, u (3), P (6), phi
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_jet192_fp32.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2403_15773_gb300", "csrc", f)
+                  for f in ("tslb_step.cu", "tslb_internal.h")]
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(nodes: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled to `nodes`, if it was taken on the current kernel source."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    sha = re.search(r"kernel_source_sha:\s*(\w+)", txt)
+    bpn = re.search(r"dram_bytes_per_node:\s*([0-9.eE+-]+)", txt)
+    if not sha or not bpn or sha.group(1) != kernel_source_sha():
+        return None
+    return float(bpn.group(1)) * nodes
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples of one GPU during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.samples = []
+        if self.proc is None:
+            return False
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+        return False
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[5 + k].lower() == "active"})
+        pw = [float(s[3]) for s in self.samples if re.match(r"^[0-9.]+$", s[3])]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples),
+                "power_w_max": max(pw) if pw else None}
+
+
+# ----------------------------------------------------------------- workloads
+
+def workload_by_name(name: str):
+    from paper_2403_15773_gb300 import inputs
+    if name == "jet192":
+        return inputs.jet_workload()
+    if name == "jet128":
+        return inputs.jet_workload(128, 128, 256)
+    if name == "jet512":
+        return inputs.weber_sweep()[1]
+    if name == "droplet32":
+        return inputs.droplet_workload()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(w) -> str:
+    return (f"{w.kind} {w.nx}x{w.ny}x{w.nz}, faces {'/'.join(w.faces)}, omega {w.omega:.6f}, "
+            f"sigma {w.sigma:.3g}, W {w.width:g}" +
+            (f", nozzle D {w.inlet_diameter:g}, u {w.inlet_u[2]:g}, noise {w.noise_amp:g}"
+             if w.kind == "jet" else f", R {w.radius:g}"))
+
+
+# ------------------------------------------------------------- CPU oracle leg
+
+def oracle_params_of(w):
+    import oracle
+    faces = {"periodic": oracle.PERIODIC, "inlet": oracle.INLET, "outflow": oracle.OUTFLOW,
+             "free_slip": oracle.FREE_SLIP}
+    return oracle.make_params(w.nx, w.ny, w.nz, w.omega, w.sigma, 1.0 / w.width,
+                              [faces[f] for f in w.faces], w.inlet_u, w.inlet_diameter, w.inlet_cx,
+                              w.inlet_cy, w.width, w.noise_amp, w.seed, normal_eps=w.normal_eps)
+
+
+def oracle_sample_workload(w, dims=(64, 64, 32)):
+    """A bounded sample of the workload for the CPU oracle: the lower part of
+    the domain around the nozzle (same physics, fewer nodes)."""
+    from paper_2403_15773_gb300 import inputs
+    if w.kind == "jet":
+        return inputs.crop_jet(w, *dims)
+    return w
+
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    import oracle
+    s_w = oracle_sample_workload(w)
+    sim = oracle.OracleSim(oracle_params_of(s_w))
+    rho, u, phi = s_w.fields()
+    sim.set_state(rho, u, phi)
+    t0 = time.perf_counter()
+    sim.step(1)
+    one = time.perf_counter() - t0
+    n = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    sim.step(n)
+    dt = time.perf_counter() - t0
+    glups = s_w.nodes * n / dt / 1e9
+    return {"value": glups, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"FP64 oracle (paper-literal 27+7 population push), {n} steps of a "
+                      f"{s_w.nx}x{s_w.ny}x{s_w.nz} crop of the workload around the nozzle, "
+                      f"{dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_gpu(args, w, storage: str, rank: int, world: int, dist):
+    import torch
+    import paper_2403_15773_gb300 as tslb
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    sim = tslb.Simulation(w, storage=storage, stream=stream)
+    rho, u, phi = w.fields()
+    sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    sim.step(args.warmup)
+    sim.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = sim.kernel_launches
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")) if world > 1 else torch.cuda.current_device())
+    with sampler:
+        barrier()
+        start.record(stream)
+        sim.step(args.steps)
+        stop.record(stream)
+        stop.synchronize()
+        barrier()
+    ms = start.elapsed_time(stop)
+    launches = sim.kernel_launches - launches0
+    m, p = sim.sums()
+    ok = math.isfinite(m) and math.isfinite(p)
+    # max over ranks of the device time
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sim.close()
+    return {"ms": ms, "launches": launches, "clocks": sampler.summary(), "finite": ok}
+
+
+def run_e2e(args, w, storage: str):
+    """Same metric through the public C ABI with host buffers: upload the
+    initial fields from pinned memory, run the steps, read the moments, the
+    phase field and the FP64 sums back into pinned memory."""
+    import torch
+    import paper_2403_15773_gb300 as tslb
+    stream = torch.cuda.Stream()
+    sim = tslb.Simulation(w, storage=storage, stream=stream)
+    N = w.nodes
+    rho, u, phi = (torch.from_numpy(a.astype(np.float32).reshape(-1)).pin_memory() for a in w.fields())
+    out_rho = torch.empty(N, dtype=torch.float32).pin_memory()
+    out_u = torch.empty(3 * N, dtype=torch.float32).pin_memory()
+    out_pi = torch.empty(6 * N, dtype=torch.float32).pin_memory()
+    out_phi = torch.empty(N, dtype=torch.float32).pin_memory()
+    # warm-up of the whole path (graph capture, first-touch of pinned pages)
+    sim.set_state_host(rho, u, phi)
+    sim.step(min(args.warmup, 16))
+    sim.moments_host(out_rho, out_u, out_pi)
+    sim.phi_host(out_phi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_state_host(rho, u, phi)
+    sim.step(args.steps)
+    sim.moments_host(out_rho, out_u, out_pi)
+    sim.phi_host(out_phi)
+    m, p = sim.sums()
+    dt = time.perf_counter() - t0
+    sim.close()
+    h2d = 5 * N * 4
+    d2h = 11 * N * 4 + 16
+    return {"value": N * args.steps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+            "note": "one job per timed region: set_state from pinned host buffers, the steps, "
+                    "get_moments + get_phi into pinned host buffers, FP64 sums; bytes per step "
+                    "are the job's copies divided by the steps"}
+
+
+def variant_line(args, w, storage, res):
+    glups = w.nodes * args.steps / (res["ms"] * 1e-3) / 1e9
+    bpn = FIELDS * 2 * (4 if storage == "fp32" else 2)
+    peak, _ = measured_peaks()
+    ach = bpn * w.nodes / (res["ms"] * 1e-3 / args.steps) / 1e9
+    return {"storage": storage, "value": glups, "unit": UNIT, "ms_per_step": res["ms"] / args.steps,
+            "bytes_per_node": bpn, "hbm_frac": ach / peak}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="tslb", choices=["tslb", "reference"])
+    ap.add_argument("--workload", default="jet192")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--variants", default="fp16,bf16",
+                    help="extra storage forms measured on the same workload ('' for none)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    w = workload_by_name(args.workload)
+
+    if args.impl == "reference":
+        # the reference arm is the FP64 CPU oracle; under torchrun only rank 0 runs it
+        if rank != 0:
+            return
+        return reference_arm(args, w)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    import paper_2403_15773_gb300 as tslb
+    tslb.lib()  # build / load the CUDA library before timing
+
+    res = run_gpu(args, w, args.storage, rank, world, dist)
+    variants = {}
+    for v in [s for s in args.variants.split(",") if s and s != args.storage]:
+        r = run_gpu(args, w, v, rank, world, dist)
+        variants[v] = variant_line(args, w, v, r)
+    e2e = None if args.no_e2e else run_e2e(args, w, args.storage)
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    nodes_total = w.nodes * world
+    sec = res["ms"] * 1e-3
+    glups = nodes_total * args.steps / sec / 1e9
+    bpn = FIELDS * 2 * (4 if args.storage == "fp32" else 2)
+    per_launch = sec / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = bpn * w.nodes / per_launch / 1e9
+    traffic = profiled_traffic(w.nodes)
+    line = {
+        "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.storage == "fp32" else "f32 (" + args.storage + " storage)",
+        "data": "synthetic",
+        "config": {"workload": describe(w), "nodes_per_gpu": w.nodes, "storage": args.storage,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": f"state {bpn * w.nodes / 1e9:.2f} GB (two buffers) > 126 MB L2: "
+                         "inputs larger than L2, no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "note": f"{bpn} algorithmic bytes per node ({FIELDS} stored values read and "
+                             f"written) x {w.nodes} nodes per launch / mean launch time; peak "
+                             f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+        "variants": variants,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if not res["finite"]:
+        line["error"] = "non-finite sums"
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, w):
+    """The FP64 CPU oracle timed as it stands on the host cores: each benchmark
+    step is one oracle time step of a bounded sample of the workload."""
+    import oracle
+    s_w = oracle_sample_workload(w, (32, 32, 32))
+    sim = oracle.OracleSim(oracle_params_of(s_w))
+    rho, u, phi = s_w.fields()
+    sim.set_state(rho, u, phi)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = s_w.nodes * args.steps / dt / 1e9
+    cb = {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+          "sample": f"{s_w.nx}x{s_w.ny}x{s_w.nz} crop of the workload around the nozzle per step"}
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": describe(w), "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

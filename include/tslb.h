@@ -1,0 +1,179 @@
+/*
+ * tslb.h - C ABI of the GB300 (sm_103a) multicomponent thread-safe lattice
+ * Boltzmann library (arXiv 2403.15773, Montessori, Hegele, Lauricella).
+ *
+ * The library advances the fused per-time-step update of the paper: a D3Q27
+ * flow solver with third-order Hermite equilibria and recursive third-order
+ * regularisation (Sec. 2, Eq. fullstrcoll, eqts, noneqts), coupled to a D3Q7
+ * conservative phase-field solver with anti-diffusion and continuum-surface
+ * surface tension (Sec. 2.2, Eq. intcapturing, antidiff).  As in the paper,
+ * the state is stored as moments only (Sec. 2: rho, rho u and the six
+ * components of Pi^neq per node, plus the phase field phi), and each step
+ * rebuilds every node's post-streamed populations from its neighbours'
+ * moments (Sec. 2, Fig. 1).  One CUDA kernel launch performs one time step.
+ *
+ * Conventions used by every entry point:
+ *   - Grid arrays are structure-of-arrays, x fastest: node n = x + nx*(y + ny*z),
+ *     N = nx*ny*nz.  Vectors are 3 blocks of N (x, y, z); the second-order
+ *     tensor P is 6 blocks of N in the order xx, yy, zz, xy, xz, yz.
+ *   - Moments exchanged with the caller: rho; u = j / rho (the velocity of the
+ *     stored momentum, before the half-force shift of the forcing scheme);
+ *     P = Pi - rho cs2 I - rho u u (the non-equilibrium momentum flux of
+ *     Sec. 2 relative to u); phi in [-1, 1], +1 = component A.
+ *   - on_device != 0: the pointer is CUDA device memory of the context's
+ *     device; 0: host memory (pageable or pinned).
+ *   - All work is issued on the context's stream; calls that return data to
+ *     the host synchronise that stream.  A context must not be used from two
+ *     host threads at once.
+ *   - Errors are returned as tslb_status; no call aborts or throws.
+ *     tslb_last_error() gives a message for the last failing call.
+ */
+#ifndef TSLB_H
+#define TSLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TSLB_API __attribute__((visibility("default")))
+#else
+#define TSLB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tslb_ctx tslb_ctx;
+
+typedef enum {
+    TSLB_OK = 0,
+    TSLB_ERR_INVALID_ARG = 1, /* bad size, pointer, parameter or boundary spec */
+    TSLB_ERR_OOM = 2,         /* device or host allocation failed / workspace too small */
+    TSLB_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    TSLB_ERR_UNSTABLE = 4,    /* the total mass or phase field became non-finite */
+    TSLB_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    TSLB_ERR_STATE = 6        /* call out of order (e.g. tslb_step before tslb_set_state) */
+} tslb_status;
+
+typedef enum { TSLB_LATTICE_D3Q27_D3Q7 = 0 } tslb_lattice;
+
+/* Storage of the 11 per-node fields in HBM.  All arithmetic is FP32. */
+typedef enum { TSLB_FP32 = 0, TSLB_FP16 = 1, TSLB_BF16 = 2 } tslb_storage;
+
+/* Face rules.  INLET is allowed on the -z face only. */
+typedef enum {
+    TSLB_BC_PERIODIC = 0,  /* wrap; both faces of an axis must be periodic */
+    TSLB_BC_INLET = 1,     /* jet inlet: ghost with rho and P of the adjacent fluid node and
+                              imposed u, phi (non-equilibrium extrapolation, Eq. original_neq) */
+    TSLB_BC_OUTFLOW = 2,   /* zero-gradient copy of the adjacent fluid node */
+    TSLB_BC_FREE_SLIP = 3  /* specular mirror about the half-way plane */
+} tslb_bc;
+
+typedef struct {
+    int32_t nx, ny, nz; /* nodes per axis; >= 1 on periodic axes, >= 2 otherwise */
+} tslb_grid;
+
+/* Boundary specification.  The inlet imposes on the -z face a smoothed top
+ * hat of diameter inlet_diameter centred at (inlet_cx, inlet_cy):
+ *   phi_B = -tanh(2 (r - D/2) / W), u_B = s (inlet_u + xi), s = (1 + phi_B)/2,
+ *   xi_c = noise_amp |inlet_u| (2 r_c - 1), r_c = (philox4x32_10_c >> 8) 2^-24,
+ * with Philox4x32-10 (Salmon et al., SC'11) on counter (x + nx y, t_lo, t_hi, 0)
+ * and key (seed_lo, seed_hi), t the step index. */
+typedef struct {
+    int32_t face[6]; /* tslb_bc for -x, +x, -y, +y, -z, +z */
+    float inlet_u[3];
+    float inlet_diameter;
+    float inlet_cx, inlet_cy;
+    float noise_amp;
+    uint64_t seed;
+} tslb_boundary;
+
+typedef struct {
+    int32_t storage;        /* tslb_storage; default TSLB_FP32 */
+    float interface_width;  /* W: anti-diffusion Gamma = 1/W gives a tanh(2x/W) interface; default 3 */
+    float normal_eps;       /* the interface normal is grad phi / sqrt(|grad phi|^2 + eps^2); default 1e-2 */
+    float field_scale[4];   /* 16-bit storage: stored value = scale * (rho - 1), scale * u,
+                               scale * P, scale * phi; 0 = default (1/(3 U^2), 1/(2 U), 1e3, 1) */
+    int32_t check_every;    /* tslb_step checks the FP64 sums for non-finite values every this
+                               many steps (synchronises); 0 = never (default) */
+    int32_t tile_z;         /* z extent of one thread block's slab; 0 = automatic */
+    int32_t graph_steps;    /* steps per captured CUDA graph replayed by tslb_step; 0 = automatic,
+                               1 = plain launches */
+    void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
+                               (blocking, so ordered with the legacy default stream) */
+} tslb_options;
+
+/* Fills *opt with the defaults above. */
+TSLB_API void tslb_default_options(tslb_options* opt);
+
+/* Bytes of device workspace tslb_init needs for this grid and options (the two
+ * state buffers, the per-block FP64 partial sums and a few counters), or 0 if
+ * the arguments are invalid. */
+TSLB_API size_t tslb_workspace_bytes(const tslb_grid* grid, const tslb_options* opt);
+
+/* Creates a context on the current CUDA device.
+ *   omega: BGK relaxation frequency in (0, 2); nu = (1/3)(1/omega - 1/2) (Sec. 2).
+ *   sigma: surface tension >= 0 (Sec. 2.2: F = -(sigma/2) kappa grad phi for phi in [-1, 1]).
+ *   bc:    face rules and inlet; NULL = fully periodic.
+ *   opt:   NULL = defaults.
+ *   workspace: device memory of at least tslb_workspace_bytes() bytes, 256-byte
+ *          aligned, owned by the caller and kept alive until tslb_destroy; NULL =
+ *          the library allocates (cudaMalloc) and frees it.
+ * The state is undefined until tslb_set_state. */
+TSLB_API tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattice, double omega,
+                      double sigma, const tslb_boundary* bc, const tslb_options* opt,
+                      void* workspace, size_t workspace_bytes);
+
+/* Sets the state from rho[N], u[3N] and phi[N]; pi[6N] sets P (NULL = 0, i.e.
+ * the populations start at the third-order equilibrium).  Step index := 0. */
+TSLB_API tslb_status tslb_set_state(tslb_ctx* ctx, const float* rho, const float* u, const float* pi,
+                           const float* phi, int on_device);
+
+/* Advances n >= 0 time steps (asynchronous on the context stream unless
+ * check_every > 0).  Each step: one fused kernel (Sec. 2, Eq. fullstrcoll with
+ * the third-order terms of Eq. eqts/noneqts, and the D3Q7 update of Eq.
+ * intcapturing/antidiff) plus, inside it, the FP64 per-block partial sums of
+ * rho and phi of the new state. */
+TSLB_API tslb_status tslb_step(tslb_ctx* ctx, int64_t n);
+
+/* Copies the current moments out (rho[N], u[3N], pi[6N]; any may be NULL). */
+TSLB_API tslb_status tslb_get_moments(tslb_ctx* ctx, float* rho, float* u, float* pi, int on_device);
+
+/* Copies the current phase field out (phi[N]). */
+TSLB_API tslb_status tslb_get_phi(tslb_ctx* ctx, float* phi, int on_device);
+
+/* Total mass sum(rho) and total phase field sum(phi) of the current state in
+ * FP64, reduced in a fixed order (bitwise reproducible).  Returns
+ * TSLB_ERR_UNSTABLE (and still the values) if either is not finite. */
+TSLB_API tslb_status tslb_sums(tslb_ctx* ctx, double* mass, double* phi_total);
+
+/* Number of steps taken since tslb_set_state / tslb_put_state. */
+TSLB_API tslb_status tslb_get_time(const tslb_ctx* ctx, int64_t* t);
+
+/* Checkpoint: the raw stored fields (11 N values of the storage type) plus
+ * the step index, tslb_state_bytes() bytes in total.  put_state restores a
+ * buffer written by get_state of a context with the same grid and storage. */
+TSLB_API size_t tslb_state_bytes(const tslb_ctx* ctx);
+TSLB_API tslb_status tslb_get_state(tslb_ctx* ctx, void* dst, int on_device);
+TSLB_API tslb_status tslb_put_state(tslb_ctx* ctx, const void* src, int on_device);
+
+/* Blocks until all work of the context has finished. */
+TSLB_API tslb_status tslb_synchronize(tslb_ctx* ctx);
+
+/* Frees the context (and the workspace if the library allocated it). */
+TSLB_API tslb_status tslb_destroy(tslb_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing tslb_init
+ * when ctx is NULL).  Never NULL. */
+TSLB_API const char* tslb_last_error(const tslb_ctx* ctx);
+TSLB_API const char* tslb_status_string(tslb_status s);
+
+/* Number of step-kernel launches issued by this context so far (each launch
+ * is one time step over the whole grid). */
+TSLB_API int64_t tslb_kernel_launches(const tslb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

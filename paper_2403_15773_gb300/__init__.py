@@ -1,0 +1,354 @@
+"""Python binding of the GB300 multicomponent thread-safe lattice Boltzmann
+library (arXiv 2403.15773).
+
+The binding only marshals arguments: every step of the method runs in the
+CUDA kernels of ``_build/libtslb.so`` behind the C ABI of ``include/tslb.h``.
+The functions ``tslb_*`` below carry the names of the C entry points;
+:class:`Simulation` is a convenience wrapper that keeps the device workspace
+in a PyTorch tensor and issues work on a PyTorch stream.
+
+There is no CPU fallback: if the CUDA library cannot be built or loaded, the
+functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "TSLB_OK", "TslbError", "Grid", "Boundary", "Options", "lib", "library_path",
+    "tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_set_state", "tslb_step",
+    "tslb_get_moments", "tslb_get_phi", "tslb_sums", "tslb_get_time", "tslb_state_bytes",
+    "tslb_get_state", "tslb_put_state", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
+    "tslb_status_string", "tslb_kernel_launches", "Simulation", "SYMBOLS",
+]
+
+TSLB_OK, TSLB_ERR_INVALID_ARG, TSLB_ERR_OOM, TSLB_ERR_CUDA, TSLB_ERR_UNSTABLE, TSLB_ERR_TIMEOUT, \
+    TSLB_ERR_STATE = range(7)
+TSLB_LATTICE_D3Q27_D3Q7 = 0
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+FACES = {"periodic": 0, "inlet": 1, "outflow": 2, "free_slip": 3}
+
+SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_set_state", "tslb_step",
+           "tslb_get_moments", "tslb_get_phi", "tslb_sums", "tslb_get_time", "tslb_state_bytes",
+           "tslb_get_state", "tslb_put_state", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
+           "tslb_status_string", "tslb_kernel_launches")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class Boundary(ctypes.Structure):
+    _fields_ = [("face", ctypes.c_int32 * 6), ("inlet_u", ctypes.c_float * 3),
+                ("inlet_diameter", ctypes.c_float), ("inlet_cx", ctypes.c_float),
+                ("inlet_cy", ctypes.c_float), ("noise_amp", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("interface_width", ctypes.c_float),
+                ("normal_eps", ctypes.c_float), ("field_scale", ctypes.c_float * 4),
+                ("check_every", ctypes.c_int32), ("tile_z", ctypes.c_int32),
+                ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
+class TslbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tslb status {status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            P, VP = ctypes.POINTER, ctypes.c_void_p
+            L.tslb_default_options.argtypes = [P(Options)]
+            L.tslb_default_options.restype = None
+            L.tslb_workspace_bytes.argtypes = [P(Grid), P(Options)]
+            L.tslb_workspace_bytes.restype = ctypes.c_size_t
+            L.tslb_init.argtypes = [P(VP), P(Grid), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    P(Boundary), P(Options), VP, ctypes.c_size_t]
+            L.tslb_set_state.argtypes = [VP, VP, VP, VP, VP, ctypes.c_int]
+            L.tslb_step.argtypes = [VP, ctypes.c_int64]
+            L.tslb_get_moments.argtypes = [VP, VP, VP, VP, ctypes.c_int]
+            L.tslb_get_phi.argtypes = [VP, VP, ctypes.c_int]
+            L.tslb_sums.argtypes = [VP, P(ctypes.c_double), P(ctypes.c_double)]
+            L.tslb_get_time.argtypes = [VP, P(ctypes.c_int64)]
+            L.tslb_state_bytes.argtypes = [VP]
+            L.tslb_state_bytes.restype = ctypes.c_size_t
+            L.tslb_get_state.argtypes = [VP, VP, ctypes.c_int]
+            L.tslb_put_state.argtypes = [VP, VP, ctypes.c_int]
+            L.tslb_synchronize.argtypes = [VP]
+            L.tslb_destroy.argtypes = [VP]
+            L.tslb_last_error.argtypes = [VP]
+            L.tslb_last_error.restype = ctypes.c_char_p
+            L.tslb_status_string.argtypes = [ctypes.c_int]
+            L.tslb_status_string.restype = ctypes.c_char_p
+            L.tslb_kernel_launches.argtypes = [VP]
+            L.tslb_kernel_launches.restype = ctypes.c_int64
+            for name in ("tslb_init", "tslb_set_state", "tslb_step", "tslb_get_moments", "tslb_get_phi",
+                         "tslb_sums", "tslb_get_time", "tslb_get_state", "tslb_put_state",
+                         "tslb_synchronize", "tslb_destroy"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int, ctx=None):
+    if status != TSLB_OK:
+        msg = lib().tslb_last_error(ctx)
+        raise TslbError(status, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- C names
+
+def tslb_default_options() -> Options:
+    o = Options()
+    lib().tslb_default_options(ctypes.byref(o))
+    return o
+
+
+def tslb_workspace_bytes(grid: Grid, opt: Optional[Options] = None) -> int:
+    return int(lib().tslb_workspace_bytes(ctypes.byref(grid), ctypes.byref(opt) if opt else None))
+
+
+def tslb_init(grid: Grid, omega: float, sigma: float, bc: Optional[Boundary] = None,
+              opt: Optional[Options] = None, workspace: int = 0, workspace_bytes: int = 0) -> int:
+    ctx = ctypes.c_void_p()
+    st = lib().tslb_init(ctypes.byref(ctx), ctypes.byref(grid), TSLB_LATTICE_D3Q27_D3Q7, float(omega),
+                         float(sigma), ctypes.byref(bc) if bc else None, ctypes.byref(opt) if opt else None,
+                         ctypes.c_void_p(workspace or None), ctypes.c_size_t(workspace_bytes))
+    _check(st, None)
+    return ctx.value
+
+
+def tslb_set_state(ctx: int, rho: int, u: int, pi: int, phi: int, on_device: int):
+    _check(lib().tslb_set_state(ctx, rho, u, pi or None, phi, int(on_device)), ctx)
+
+
+def tslb_step(ctx: int, n: int):
+    _check(lib().tslb_step(ctx, int(n)), ctx)
+
+
+def tslb_get_moments(ctx: int, rho: int, u: int, pi: int, on_device: int):
+    _check(lib().tslb_get_moments(ctx, rho or None, u or None, pi or None, int(on_device)), ctx)
+
+
+def tslb_get_phi(ctx: int, phi: int, on_device: int):
+    _check(lib().tslb_get_phi(ctx, phi, int(on_device)), ctx)
+
+
+def tslb_sums(ctx: int):
+    m, p = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tslb_sums(ctx, ctypes.byref(m), ctypes.byref(p)), ctx)
+    return m.value, p.value
+
+
+def tslb_get_time(ctx: int) -> int:
+    t = ctypes.c_int64()
+    _check(lib().tslb_get_time(ctx, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def tslb_state_bytes(ctx: int) -> int:
+    return int(lib().tslb_state_bytes(ctx))
+
+
+def tslb_get_state(ctx: int, dst: int, on_device: int):
+    _check(lib().tslb_get_state(ctx, dst, int(on_device)), ctx)
+
+
+def tslb_put_state(ctx: int, src: int, on_device: int):
+    _check(lib().tslb_put_state(ctx, src, int(on_device)), ctx)
+
+
+def tslb_synchronize(ctx: int):
+    _check(lib().tslb_synchronize(ctx), ctx)
+
+
+def tslb_destroy(ctx: int):
+    _check(lib().tslb_destroy(ctx), None)
+
+
+def tslb_last_error(ctx: Optional[int]) -> str:
+    m = lib().tslb_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def tslb_status_string(status: int) -> str:
+    return lib().tslb_status_string(int(status)).decode()
+
+
+def tslb_kernel_launches(ctx: int) -> int:
+    return int(lib().tslb_kernel_launches(ctx))
+
+
+# ------------------------------------------------------------ convenience
+
+def _boundary_from(workload) -> Boundary:
+    b = Boundary()
+    for k, f in enumerate(workload.faces):
+        b.face[k] = FACES[f]
+    for a in range(3):
+        b.inlet_u[a] = float(workload.inlet_u[a])
+    b.inlet_diameter = float(workload.inlet_diameter)
+    b.inlet_cx = float(workload.inlet_cx)
+    b.inlet_cy = float(workload.inlet_cy)
+    b.noise_amp = float(workload.noise_amp)
+    b.seed = int(workload.seed)
+    return b
+
+
+class Simulation:
+    """One simulation context on the current CUDA device.
+
+    ``workload`` is an :class:`inputs.Workload` (grid, omega, sigma, faces,
+    inlet).  The workspace is a torch uint8 tensor owned by this object; work
+    is issued on ``stream`` (a ``torch.cuda.Stream``; default: a new one).
+    """
+
+    def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
+                 graph_steps: int = 0, check_every: int = 0, field_scale=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Simulation needs a CUDA device")
+        self.workload = workload
+        self.grid = Grid(workload.nx, workload.ny, workload.nz)
+        self.N = workload.nx * workload.ny * workload.nz
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        o = tslb_default_options()
+        o.storage = STORAGE[storage]
+        o.interface_width = float(workload.width)
+        o.normal_eps = float(getattr(workload, "normal_eps", 1e-2))
+        o.tile_z = int(tile_z)
+        o.graph_steps = int(graph_steps)
+        o.check_every = int(check_every)
+        if field_scale is not None:
+            for g in range(4):
+                o.field_scale[g] = float(field_scale[g])
+        o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self.options = o
+        nbytes = tslb_workspace_bytes(self.grid, o)
+        if nbytes == 0:
+            raise TslbError(TSLB_ERR_INVALID_ARG, "invalid grid or options")
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self._ws.data_ptr()
+        off = (-base) % 256
+        self.ctx = tslb_init(self.grid, workload.omega, workload.sigma, _boundary_from(workload), o,
+                             base + off, nbytes)
+
+    # -- state
+    def set_state(self, rho, u, phi, pi=None):
+        """rho[N], u[3, N], phi[N] (torch tensors on any device, or numpy)."""
+        import torch
+        dev = torch.device("cuda")
+
+        def prep(a, n):
+            if a is None:
+                return None
+            t = torch.as_tensor(a)
+            t = t.to(device=dev, dtype=torch.float32).contiguous().reshape(-1)
+            if t.numel() != n:
+                raise ValueError(f"expected {n} values, got {t.numel()}")
+            return t
+
+        N = self.N
+        r, uu, ph, pp = prep(rho, N), prep(u, 3 * N), prep(phi, N), prep(pi, 6 * N)
+        torch.cuda.current_stream().synchronize()  # inputs written on the current stream
+        tslb_set_state(self.ctx, r.data_ptr(), uu.data_ptr(), pp.data_ptr() if pp is not None else 0,
+                       ph.data_ptr(), 1)
+        self.stream.synchronize()  # the temporaries above may be freed after this
+
+    def set_state_host(self, rho, u, phi, pi=None):
+        """Host (numpy / CPU tensor, pinned or pageable) inputs through the C ABI."""
+        ptr = lambda a: a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        tslb_set_state(self.ctx, ptr(rho), ptr(u), ptr(pi) if pi is not None else 0, ptr(phi), 0)
+
+    def step(self, n: int = 1):
+        tslb_step(self.ctx, n)
+
+    def moments(self):
+        """(rho[N], u[3, N], pi[6, N]) as float32 CUDA tensors."""
+        import torch
+        N = self.N
+        rho = torch.empty(N, dtype=torch.float32, device="cuda")
+        u = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+        pi = torch.empty(6 * N, dtype=torch.float32, device="cuda")
+        tslb_get_moments(self.ctx, rho.data_ptr(), u.data_ptr(), pi.data_ptr(), 1)
+        return rho, u.view(3, N), pi.view(6, N)
+
+    def moments_host(self, rho, u, pi):
+        ptr = lambda a: (a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data) if a is not None else 0
+        tslb_get_moments(self.ctx, ptr(rho), ptr(u), ptr(pi), 0)
+
+    def phi(self):
+        import torch
+        out = torch.empty(self.N, dtype=torch.float32, device="cuda")
+        tslb_get_phi(self.ctx, out.data_ptr(), 1)
+        return out
+
+    def phi_host(self, phi):
+        tslb_get_phi(self.ctx, phi.data_ptr() if hasattr(phi, "data_ptr") else phi.ctypes.data, 0)
+
+    def fields_numpy(self):
+        """(rho, u, pi, phi) as float64 numpy arrays shaped like the grid."""
+        rho, u, pi = self.moments()
+        ph = self.phi()
+        s = (self.workload.nz, self.workload.ny, self.workload.nx)
+        f = lambda t, lead: t.double().cpu().numpy().reshape(lead + s)
+        return f(rho, ()), f(u, (3,)), f(pi, (6,)), f(ph, ())
+
+    def sums(self):
+        return tslb_sums(self.ctx)
+
+    @property
+    def t(self) -> int:
+        return tslb_get_time(self.ctx)
+
+    @property
+    def kernel_launches(self) -> int:
+        return tslb_kernel_launches(self.ctx)
+
+    def state_bytes(self) -> int:
+        return tslb_state_bytes(self.ctx)
+
+    def get_state(self):
+        import torch
+        buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device="cuda")
+        tslb_get_state(self.ctx, buf.data_ptr(), 1)
+        return buf
+
+    def put_state(self, buf):
+        tslb_put_state(self.ctx, buf.data_ptr(), 1 if buf.is_cuda else 0)
+
+    def synchronize(self):
+        tslb_synchronize(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            tslb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

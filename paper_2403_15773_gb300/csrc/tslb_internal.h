@@ -1,0 +1,68 @@
+// Internal interface between the C-ABI host code (tslb_api.cu) and the CUDA
+// kernels (tslb_step.cu) of the TSLB library.  Not installed, not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tslb {
+
+enum { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTFLOW = 2, BC_FREE_SLIP = 3 };
+enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
+
+// Stored fields of one state buffer, each a block of `fstride` elements:
+// rho - 1, u (3), P (xx, yy, zz, xy, xz, yz), phi.
+enum {
+    F_DRHO = 0, F_UX, F_UY, F_UZ, F_PXX, F_PYY, F_PZZ, F_PXY, F_PXZ, F_PYZ, F_PHI, NFIELDS
+};
+
+// Everything the step kernel needs, passed by value (__grid_constant__).
+struct StepParams {
+    int nx, ny, nz;
+    int face[6];
+    int tile_z;
+    long long fstride;       // elements between consecutive fields of a buffer
+    float omega, sigma, gamma, normal_eps2;
+    float inlet_u[3], inlet_umag, inlet_half_d, inlet_cx, inlet_cy, inlet_two_over_w, noise_amp;
+    unsigned seed_lo, seed_hi;
+    float scale[NFIELDS];    // 16-bit storage: stored = scale * value
+    float inv_scale[NFIELDS];
+};
+
+struct LaunchShape {
+    dim3 grid, block;
+    size_t smem;
+    int nw;                  // warps per block (rows of a tile incl. 2 halo rows)
+};
+
+// Geometry of the step kernel launch for this grid (tile_z = z slab per block).
+LaunchShape step_shape(const StepParams& p, int storage);
+
+// One time step: state `in` (step index *t_in) -> state `out` (*t_out = *t_in + 1),
+// per-block FP64 partial sums (sum rho, sum phi) into partials[2 * block].
+cudaError_t launch_step(const StepParams& p, int storage, const void* in, void* out,
+                        const long long* t_in, long long* t_out, double* partials,
+                        cudaStream_t s);
+
+// Kernel attributes (dynamic shared memory) of the step kernel; once per device.
+cudaError_t prepare_kernels(int storage);
+
+// One caller field (float, device) -> one stored field (rho - 1 for F_DRHO).
+cudaError_t launch_put_field(const StepParams& p, int storage, const float* src, int field,
+                             void* state, cudaStream_t s);
+
+// One stored field -> float moment (rho for F_DRHO, the value itself otherwise).
+cudaError_t launch_get_field(const StepParams& p, int storage, const void* state, int field,
+                             float* dst, cudaStream_t s);
+
+// Partial sums of a stored state (used when no step has produced them).
+cudaError_t launch_state_sums(const StepParams& p, int storage, const void* state,
+                              double* partials, int* nparts, cudaStream_t s);
+
+// Fixed-order FP64 reduction of n partial pairs into result[0..1].
+cudaError_t launch_finish_sums(const double* partials, int n, double* result, cudaStream_t s);
+
+// Largest number of partial pairs any launch above writes for this grid.
+int max_partials(const StepParams& p, int storage);
+
+}  // namespace tslb

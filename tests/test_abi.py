@@ -1,0 +1,101 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/tslb.h; host-side argument checking works without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2403_15773_gb300 as tslb
+from paper_2403_15773_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"TSLB_API\s+[\w\s\*]*?\b(tslb_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_abi():
+    names = declared_symbols()
+    for n in ("tslb_init", "tslb_step", "tslb_get_moments", "tslb_get_phi", "tslb_sums", "tslb_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    L = ctypes.CDLL(path)
+    for n in declared_symbols():
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (tslb_\w+)", out))
+    assert set(declared_symbols()) <= exported
+
+
+def test_binding_names_match_header():
+    assert sorted(tslb.SYMBOLS) == declared_symbols()
+    for n in declared_symbols():
+        assert callable(getattr(tslb, n))
+
+
+def test_default_options():
+    o = tslb.tslb_default_options()
+    assert o.storage == 0 and abs(o.interface_width - 3.0) < 1e-7 and abs(o.normal_eps - 1e-2) < 1e-9
+    assert o.check_every == 0 and o.tile_z == 0 and o.graph_steps == 0
+
+
+def test_workspace_bytes():
+    g = tslb.Grid(32, 32, 32)
+    b = tslb.tslb_workspace_bytes(g)
+    N = 32 ** 3
+    assert b >= 2 * 11 * N * 4 + N * 4
+    o = tslb.tslb_default_options()
+    o.storage = tslb.STORAGE["fp16"]
+    b16 = tslb.tslb_workspace_bytes(g, o)
+    assert 2 * 11 * N * 2 <= b16 < b
+    assert tslb.tslb_workspace_bytes(tslb.Grid(0, 4, 4)) == 0
+
+
+def _bc(faces):
+    b = tslb.Boundary()
+    for k, f in enumerate(faces):
+        b.face[k] = tslb.FACES[f]
+    return b
+
+
+@pytest.mark.parametrize("case", [
+    dict(omega=2.5),
+    dict(omega=0.0),
+    dict(sigma=-1.0),
+    dict(faces=("inlet", "outflow", "periodic", "periodic", "periodic", "periodic")),
+    dict(faces=("periodic", "outflow", "periodic", "periodic", "periodic", "periodic")),
+    dict(grid=(1, 8, 8), faces=("free_slip", "free_slip", "periodic", "periodic", "periodic", "periodic")),
+    dict(grid=(8, 8, 0)),
+])
+def test_init_rejects_invalid_arguments_before_touching_the_gpu(case):
+    g = tslb.Grid(*case.get("grid", (8, 8, 8)))
+    bc = _bc(case.get("faces", ("periodic",) * 6))
+    with pytest.raises(tslb.TslbError) as ei:
+        tslb.tslb_init(g, case.get("omega", 1.5), case.get("sigma", 0.0), bc)
+    assert ei.value.status == tslb.TSLB_ERR_INVALID_ARG
+    assert tslb.tslb_last_error(None)
+
+
+def test_status_strings():
+    assert tslb.tslb_status_string(0) == "ok"
+    assert "invalid" in tslb.tslb_status_string(1)
+
+
+def test_product_code_does_not_use_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2403_15773_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
+                src = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in src and "tslb_oracle" not in src, fn

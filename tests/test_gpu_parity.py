@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Error norm (max over the grid): rho relative to max|rho|, u relative to
+max(max|u|, 0.05) (the jet speed), phi absolute (phi in [-1, 1]).  The FP32
+step must match the oracle to 1e-5 after 100 steps."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2403_15773_gb300 as tslb
+from paper_2403_15773_gb300 import inputs
+from _util import oracle_params, oracle_sim
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def gpu_run(w, steps, fields=None, storage="fp32", pi=None, **kw):
+    rho, u, phi = w.fields() if fields is None else fields
+    sim = tslb.Simulation(w, storage=storage, **kw)
+    sim.set_state(torch.from_numpy(np.asarray(rho)), torch.from_numpy(np.asarray(u)),
+                  torch.from_numpy(np.asarray(phi)), None if pi is None else torch.from_numpy(pi))
+    sim.step(steps)
+    out = sim.fields_numpy()
+    sums = sim.sums()
+    launches = sim.kernel_launches
+    sim.close()
+    return out, sums, launches
+
+
+def errors(g, r):
+    e_rho = np.max(np.abs(g[0] - r[0])) / np.max(np.abs(r[0]))
+    e_u = np.max(np.abs(g[1] - r[1])) / max(np.max(np.abs(r[1])), 0.05)
+    e_phi = np.max(np.abs(g[3] - r[3]))
+    return e_rho, e_u, e_phi
+
+
+def check_parity(w, steps, fields=None, pi=None):
+    g, sums, launches = gpu_run(w, steps, fields, pi=pi)
+    s = oracle_sim(w, fields=fields) if pi is None else None
+    if s is None:
+        s = oracle.OracleSim(oracle_params(w))
+        rho, u, phi = fields
+        s.set_state(rho, u, phi, pi=pi)
+    s.step(steps)
+    r = s.moments()
+    e = errors(g, r)
+    assert launches == steps
+    assert max(e) < TOL, f"{w.name}: err rho {e[0]:.2e} u {e[1]:.2e} phi {e[2]:.2e}"
+    # P is a small quantity; compare it on the scale of its own magnitude
+    e_pi = np.max(np.abs(g[2] - r[2])) / max(np.max(np.abs(r[2])), 1e-8)
+    assert e_pi < 1e-3, f"{w.name}: err P {e_pi:.2e}"
+    m_ref, p_ref, _ = s.sums()
+    assert abs(sums[0] - m_ref) / m_ref < 1e-6
+    assert abs(sums[1] - p_ref) / max(abs(p_ref), 1.0) < 1e-6
+    return e
+
+
+def test_droplet_32_periodic_100_steps():
+    """Static droplet: 32^3 periodic, R = 8, W = 3, omega 1.6, sigma 0.01."""
+    check_parity(inputs.droplet_workload(), 100)
+
+
+def test_jet_all_boundaries_100_steps():
+    """Free-slip sides, inlet with 1 % noise, outflow: every ghost rule."""
+    w = inputs.jet_workload(48, 40, 44, diameter=12, we=100, noise=0.01, seed=3)
+    check_parity(w, 100)
+
+
+def test_jet_crop_of_the_192x192x384_geometry():
+    """A 64^3 crop of the jet workload (D = 16, omega 1.998, sigma 4e-4, noise 1 %)."""
+    w = inputs.crop_jet(inputs.jet_workload(), 64, 64, 64)
+    check_parity(w, 100)
+
+
+def test_ragged_tiles_mixed_faces():
+    """33 x 17 x 29 (partial tiles in every direction), periodic x, free-slip y,
+    outflow on both z faces, an off-centre droplet in a random smooth flow."""
+    w = inputs.droplet_workload(8, radius=6.0)
+    w.nx, w.ny, w.nz = 33, 17, 29
+    w.faces = ("periodic", "periodic", "free_slip", "free_slip", "outflow", "outflow")
+    w.name = "ragged"
+    rho0, u0, pi0, _ = inputs.random_smooth_fields(33, 17, 29, seed=8, amp_rho=2e-3, amp_u=2e-2, amp_pi=1e-4)
+    _, _, phi = inputs.droplet_fields(33, 17, 29, 6.0, 3.0, center=(13.0, 8.0, 15.0))
+    check_parity(w, 100, fields=(rho0, u0, phi), pi=pi0)
+
+
+@pytest.mark.parametrize("dims,faces", [
+    ((48, 40, 1), ("periodic",) * 6),
+    ((2, 30, 20), ("free_slip", "free_slip", "periodic", "periodic", "outflow", "outflow")),
+    ((70, 3, 5), ("periodic", "periodic", "free_slip", "free_slip", "periodic", "periodic")),
+])
+def test_thin_and_small_grids(dims, faces):
+    nx, ny, nz = dims
+    w = inputs.droplet_workload(8, radius=5.0)
+    w.nx, w.ny, w.nz, w.faces, w.name = nx, ny, nz, faces, f"small{nx}x{ny}x{nz}"
+    rho0, u0, pi0, phi = inputs.random_smooth_fields(nx, ny, nz, seed=21, amp_rho=2e-3, amp_u=2e-2,
+                                                      amp_pi=1e-4)
+    check_parity(w, 50, fields=(rho0, u0, phi), pi=pi0)
+
+
+def test_rest_state_is_bitwise_fixed():
+    w = inputs.droplet_workload(24)
+    N = w.nodes
+    for phi0 in (1.0, -1.0):
+        g, _, _ = gpu_run(w, 40, fields=(np.ones((24, 24, 24)), np.zeros((3, 24, 24, 24)),
+                                         np.full((24, 24, 24), phi0)))
+        assert np.all(g[0] == 1.0) and np.all(g[1] == 0.0) and np.all(g[2] == 0.0)
+        assert np.all(g[3] == phi0)
+
+
+def test_conservation_on_periodic_box():
+    w = inputs.droplet_workload()
+    rho, u, phi = w.fields()
+    sim = tslb.Simulation(w)
+    sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    m0, p0 = sim.sums()
+    sim.step(200)
+    m1, p1 = sim.sums()
+    sim.close()
+    assert abs(m1 - m0) / m0 < 1e-7
+    assert abs(p1 - p0) / abs(p0) < 1e-6
+
+
+def test_deterministic_and_graph_equals_plain_launches():
+    w = inputs.jet_workload(40, 36, 30, diameter=10, noise=0.01, seed=4)
+    a, sa, _ = gpu_run(w, 37)
+    b, sb, _ = gpu_run(w, 37)
+    c, sc, _ = gpu_run(w, 37, graph_steps=1)
+    for k in range(4):
+        assert np.array_equal(a[k], b[k]) and np.array_equal(a[k], c[k])
+    assert sa == sb == sc
+
+
+@pytest.mark.parametrize("tile_z", [1, 5, 13])
+def test_fields_independent_of_tile_z(tile_z):
+    w = inputs.jet_workload(40, 36, 30, diameter=10, noise=0.01, seed=4)
+    a, _, _ = gpu_run(w, 12)
+    b, _, _ = gpu_run(w, 12, tile_z=tile_z)
+    for k in range(4):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_checkpoint_resume_bitwise():
+    w = inputs.jet_workload(40, 36, 30, diameter=10, noise=0.01, seed=6)
+    ref, _, _ = gpu_run(w, 30)
+    rho, u, phi = w.fields()
+    s1 = tslb.Simulation(w)
+    s1.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    s1.step(13)
+    ck = s1.get_state().cpu()
+    s1.close()
+    s2 = tslb.Simulation(w)
+    s2.put_state(ck)
+    assert s2.t == 13
+    s2.step(17)
+    got = s2.fields_numpy()
+    s2.close()
+    for k in range(4):
+        assert np.array_equal(ref[k], got[k])
+
+
+def test_host_buffer_path_matches_device_path():
+    w = inputs.jet_workload(40, 36, 30, diameter=10, noise=0.01, seed=6)
+    rho, u, phi = (a.astype(np.float32) for a in w.fields())
+    a, _, _ = gpu_run(w, 10)
+    sim = tslb.Simulation(w)
+    sim.set_state_host(np.ascontiguousarray(rho), np.ascontiguousarray(u), np.ascontiguousarray(phi))
+    sim.step(10)
+    N = w.nodes
+    r, uu, pp, ph = (np.empty(N, np.float32), np.empty(3 * N, np.float32), np.empty(6 * N, np.float32),
+                     np.empty(N, np.float32))
+    sim.moments_host(r, uu, pp)
+    sim.phi_host(ph)
+    sim.close()
+    s = a[0].shape
+    assert np.array_equal(a[0], r.reshape(s).astype(np.float64))
+    assert np.array_equal(a[1], uu.reshape((3,) + s).astype(np.float64))
+    assert np.array_equal(a[2], pp.reshape((6,) + s).astype(np.float64))
+    assert np.array_equal(a[3], ph.reshape(s).astype(np.float64))
+
+
+def test_call_order_and_pointer_errors():
+    w = inputs.droplet_workload(16)
+    sim = tslb.Simulation(w)
+    with pytest.raises(tslb.TslbError) as ei:
+        sim.step(1)
+    assert ei.value.status == tslb.TSLB_ERR_STATE
+    host = np.zeros(w.nodes, np.float32)
+    with pytest.raises(tslb.TslbError) as ei:
+        tslb.tslb_set_state(sim.ctx, host.ctypes.data, host.ctypes.data, 0, host.ctypes.data, 1)
+    assert ei.value.status == tslb.TSLB_ERR_INVALID_ARG
+    sim.close()
+
+
+def test_full_size_jet_sampled_step():
+    """The 192 x 192 x 384 jet in the benchmark's launch configuration: after
+    60 steps, one more step is checked node by node against the oracle's
+    single-step evaluation at 4000 sampled nodes (boundary faces, nozzle
+    and interior) from the same stored state."""
+    w = inputs.jet_workload()
+    rho, u, phi = w.fields()
+    sim = tslb.Simulation(w)
+    sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    sim.step(60)
+    before = sim.fields_numpy()
+    t = sim.t
+    sim.step(1)
+    after = sim.fields_numpy()
+    sim.close()
+    nx, ny, nz = w.nx, w.ny, w.nz
+    rng = np.random.default_rng(0)
+    pts = [rng.integers(0, [nx, ny, nz], size=(2000, 3))]
+    for axis, val in ((0, 0), (0, nx - 1), (1, 0), (1, ny - 1), (2, 0), (2, 1), (2, nz - 1)):
+        p = rng.integers(0, [nx, ny, nz], size=(200, 3))
+        p[:, axis] = val
+        pts.append(p)
+    nozzle = np.stack([rng.integers(88, 104, 200), rng.integers(88, 104, 200), rng.integers(0, 6, 200)], 1)
+    pts.append(nozzle)
+    P = np.concatenate(pts)
+    idx = P[:, 0] + nx * (P[:, 1] + ny * P[:, 2])
+    flat = lambda a: a.reshape(a.shape[0], -1) if a.ndim == 4 else a.reshape(-1)
+    out = oracle.step_sample(oracle_params(w), t, flat(before[0]), flat(before[1]), flat(before[2]),
+                             flat(before[3]), idx)
+    g_rho, g_u, g_pi, g_phi = (flat(a) for a in after)
+    e_rho = np.max(np.abs(g_rho[idx] - out[:, 0])) / np.max(np.abs(out[:, 0]))
+    e_u = np.max(np.abs(g_u[:, idx].T - out[:, 1:4])) / max(np.max(np.abs(out[:, 1:4])), 0.05)
+    e_phi = np.max(np.abs(g_phi[idx] - out[:, 10]))
+    assert max(e_rho, e_u, e_phi) < TOL, (e_rho, e_u, e_phi)
+    e_pi = np.max(np.abs(g_pi[:, idx].T - out[:, 4:10])) / max(np.max(np.abs(out[:, 4:10])), 1e-8)
+    assert e_pi < 1e-3, e_pi
