@@ -173,6 +173,28 @@ TSLB_API const char* tslb_status_string(tslb_status s);
  * is one time step over the whole grid). */
 TSLB_API int64_t tslb_kernel_launches(const tslb_ctx* ctx);
 
+/* The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate device memory when they ask for the totals.  cudaMalloc
+ * and cudaFree synchronise the whole device, which an asynchronous pipeline
+ * cannot afford, and a process whose device memory is held by another
+ * allocator's pool may have none left to allocate; tslb_sums needs a context
+ * whose workspace had to be allocated first.
+ *
+ * Writes out[0] = sum(rho) and out[1] = sum(phi) in FP64 for the caller's FP32
+ * device arrays rho[n] and phi[n] (out: 2 doubles of device memory), reduced in
+ * a fixed order, asynchronously on cuda_stream (NULL = legacy default stream).
+ * Allocates nothing: its scratch is a fixed array of 16384 FP64 partial pairs
+ * (256 KiB) in the library's own device memory, held by every GPU that loads
+ * the library until the process exits.  n must lie in [1, 268435456] (16384
+ * partials of 16384 values; 512 x 512 x 1024 nodes); larger n returns
+ * TSLB_ERR_INVALID_ARG without launching anything.  The first call on a device
+ * looks up the scratch's device address, so make it before any stream capture.
+ * All calls share the scratch: calls whose work overlaps on the GPU race on it
+ * and must be ordered by the caller (same stream, or events).  Returns
+ * TSLB_ERR_CUDA if a launch fails; messages via tslb_last_error(NULL). */
+TSLB_API tslb_status tslb_field_sums_noalloc(const float* rho, const float* phi, int64_t n,
+                                             double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

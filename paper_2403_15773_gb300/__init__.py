@@ -26,7 +26,7 @@ __all__ = [
     "tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_set_state", "tslb_step",
     "tslb_get_moments", "tslb_get_phi", "tslb_sums", "tslb_get_time", "tslb_state_bytes",
     "tslb_get_state", "tslb_put_state", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
-    "tslb_status_string", "tslb_kernel_launches", "Simulation", "SYMBOLS",
+    "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc", "Simulation", "SYMBOLS",
 ]
 
 TSLB_OK, TSLB_ERR_INVALID_ARG, TSLB_ERR_OOM, TSLB_ERR_CUDA, TSLB_ERR_UNSTABLE, TSLB_ERR_TIMEOUT, \
@@ -38,7 +38,7 @@ FACES = {"periodic": 0, "inlet": 1, "outflow": 2, "free_slip": 3}
 SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_set_state", "tslb_step",
            "tslb_get_moments", "tslb_get_phi", "tslb_sums", "tslb_get_time", "tslb_state_bytes",
            "tslb_get_state", "tslb_put_state", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
-           "tslb_status_string", "tslb_kernel_launches")
+           "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc")
 
 
 class Grid(ctypes.Structure):
@@ -104,6 +104,8 @@ def lib() -> ctypes.CDLL:
             L.tslb_status_string.restype = ctypes.c_char_p
             L.tslb_kernel_launches.argtypes = [VP]
             L.tslb_kernel_launches.restype = ctypes.c_int64
+            L.tslb_field_sums_noalloc.argtypes = [VP, VP, ctypes.c_int64, VP, VP]
+            L.tslb_field_sums_noalloc.restype = ctypes.c_int
             for name in ("tslb_init", "tslb_set_state", "tslb_step", "tslb_get_moments", "tslb_get_phi",
                          "tslb_sums", "tslb_get_time", "tslb_get_state", "tslb_put_state",
                          "tslb_synchronize", "tslb_destroy"):
@@ -199,6 +201,13 @@ def tslb_status_string(status: int) -> str:
 
 def tslb_kernel_launches(ctx: int) -> int:
     return int(lib().tslb_kernel_launches(ctx))
+
+
+def tslb_field_sums_noalloc(rho: int, phi: int, n: int, out: int, stream: int = 0):
+    """FP64 totals of caller-owned FP32 device fields into out[0..1] (device),
+    without any device allocation: for callers that cannot allocate at that
+    point (see include/tslb.h).  Asynchronous on `stream`."""
+    _check(lib().tslb_field_sums_noalloc(rho, phi, int(n), out, stream or None), None)
 
 
 # ------------------------------------------------------------ convenience

@@ -274,6 +274,10 @@ tslb_status finish_sums(tslb_ctx* c, double* mass, double* phi_total) {
 
 }  // namespace
 
+namespace tslb {
+void set_global_error(const char* msg) { g_init_err = msg ? msg : ""; }
+}  // namespace tslb
+
 extern "C" {
 
 void tslb_default_options(tslb_options* opt) {

@@ -65,4 +65,7 @@ cudaError_t launch_finish_sums(const double* partials, int n, double* result, cu
 // Largest number of partial pairs any launch above writes for this grid.
 int max_partials(const StepParams& p, int storage);
 
+// Message returned by tslb_last_error(NULL) (calls that have no context).
+void set_global_error(const char* msg);
+
 }  // namespace tslb
