@@ -190,9 +190,13 @@ def run_gpu(args, w, storage: str, rank: int, world: int, dist):
     import paper_2403_15773_gb300 as tslb
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream()
-    sim = tslb.Simulation(w, storage=storage, stream=stream)
+    sim = tslb.Simulation(w, storage=storage, stream=stream, block_warps=args.block_warps,
+                          tile_z=args.tile_z)
     rho, u, phi = w.fields()
     sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    shape = None
+    if not args.block_warps and not args.tile_z:
+        shape = sim.autotune(6)  # tile shape chosen by timing; the state does not change
     sim.step(args.warmup)
     sim.synchronize()
 
@@ -221,7 +225,60 @@ def run_gpu(args, w, storage: str, rank: int, world: int, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     sim.close()
-    return {"ms": ms, "launches": launches, "clocks": sampler.summary(), "finite": ok}
+    return {"ms": ms, "launches": launches, "clocks": sampler.summary(), "finite": ok,
+            "shape": {"block_warps": shape[0], "tile_z": shape[1]} if shape else
+            {"block_warps": args.block_warps or 12, "tile_z": args.tile_z or 32}}
+
+
+def run_batched(args):
+    """The ensemble of independent uneven grids advanced together (one
+    persistent launch per step, graph-replayed, autotuned tiles), against the
+    same grids advanced one after another with the plain FP32 path."""
+    import torch
+    import paper_2403_15773_gb300 as tslb
+    from paper_2403_15773_gb300 import inputs
+    ws = inputs.batched_ensemble()
+    steps = args.batch_steps
+    stream = torch.cuda.Stream()
+    b = tslb.BatchSimulation(ws, stream=stream)
+    for i, w in enumerate(ws):
+        b.set_state(i, *w.fields())
+    shape = b.autotune(3)
+    b.step(args.warmup)
+    b.synchronize()
+    st, sp = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = b.kernel_launches
+    st.record(stream)
+    b.step(steps)
+    sp.record(stream)
+    sp.synchronize()
+    ms_batch = st.elapsed_time(sp)
+    launches = b.kernel_launches - l0
+    b.close()
+    nodes = sum(w.nodes for w in ws)
+    ms_seq = 0.0
+    for w in ws:
+        s = tslb.Simulation(w, stream=stream)
+        rho, u, phi = w.fields()
+        s.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+        s.step(args.warmup)
+        s.synchronize()
+        st.record(stream)
+        s.step(steps)
+        sp.record(stream)
+        sp.synchronize()
+        ms_seq += st.elapsed_time(sp)
+        s.close()
+    g_batch = nodes * steps / (ms_batch * 1e-3) / 1e9
+    g_seq = nodes * steps / (ms_seq * 1e-3) / 1e9
+    peak, _ = measured_peaks()
+    return {"storage": "fp32", "instances": len(ws), "nodes": nodes, "steps": steps, "value": g_batch,
+            "unit": UNIT, "ms_per_step": ms_batch / steps,
+            "hbm_frac": FIELDS * 8 * nodes / (ms_batch * 1e-3 / steps) / 1e9 / peak,
+            "sequential_fp32_value": g_seq, "speedup_vs_sequential_fp32": g_batch / g_seq,
+            "gpu_launches": launches, "autotuned": {"block_warps": shape[0], "tile_z": shape[1]},
+            "workload": "64 cubic grids, edges uniform in {48, 64, 96, 128}, periodic droplets (R = edge/4) "
+                        "and jets (D = 0.15 edge, periodic sides), We log-uniform in [10, 2000], seed 4"}
 
 
 def run_e2e(args, w, storage: str):
@@ -261,13 +318,41 @@ def run_e2e(args, w, storage: str):
                     "are the job's copies divided by the steps"}
 
 
-def variant_line(args, w, storage, res):
+def variant_line(args, w, storage, res, base_glups):
     glups = w.nodes * args.steps / (res["ms"] * 1e-3) / 1e9
     bpn = FIELDS * 2 * (4 if storage == "fp32" else 2)
     peak, _ = measured_peaks()
     ach = bpn * w.nodes / (res["ms"] * 1e-3 / args.steps) / 1e9
-    return {"storage": storage, "value": glups, "unit": UNIT, "ms_per_step": res["ms"] / args.steps,
-            "bytes_per_node": bpn, "hbm_frac": ach / peak}
+    return {"storage": storage, "value": glups, "unit": UNIT, "speedup_vs_fp32": glups / base_glups,
+            "ms_per_step": res["ms"] / args.steps, "bytes_per_node": bpn, "hbm_frac": ach / peak,
+            "state_gb": bpn * w.nodes / 1e9}
+
+
+def oracle_errors(w, storages, steps=200):
+    """Max errors against the FP64 oracle of each storage form on a small crop
+    of the workload (48^3 around the nozzle, D 8), same physics."""
+    import torch
+    import oracle
+    import paper_2403_15773_gb300 as tslb
+    from paper_2403_15773_gb300 import inputs
+    c = inputs.crop_jet(w, 48, 48, 48, diameter=8) if w.kind == "jet" else w
+    rho, u, phi = c.fields()
+    ref = oracle.OracleSim(oracle_params_of(c))
+    ref.set_state(rho, u, phi)
+    ref.step(steps)
+    r = ref.moments()
+    out = {}
+    for st in storages:
+        sim = tslb.Simulation(c, storage=st)
+        sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+        sim.step(steps)
+        g = sim.fields_numpy()
+        sim.close()
+        out[st] = {"rho": float(np.max(np.abs(g[0] - r[0])) / np.max(np.abs(r[0]))),
+                   "u": float(np.max(np.abs(g[1] - r[1])) / max(np.max(np.abs(r[1])), 0.05)),
+                   "phi": float(np.max(np.abs(g[3] - r[3])))}
+    case = f"{c.nx}x{c.ny}x{c.nz} crop of the workload, {steps} steps, max error (rho / max rho, u / max(max u, 0.05), phi)"
+    return out, case
 
 
 def main():
@@ -282,6 +367,11 @@ def main():
                     help="extra storage forms measured on the same workload ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oracle-error", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--block-warps", type=int, default=0)
+    ap.add_argument("--tile-z", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -306,10 +396,20 @@ def main():
     tslb.lib()  # build / load the CUDA library before timing
 
     res = run_gpu(args, w, args.storage, rank, world, dist)
+    base_glups = w.nodes * args.steps / (res["ms"] * 1e-3) / 1e9
     variants = {}
-    for v in [s for s in args.variants.split(",") if s and s != args.storage]:
+    vlist = [s for s in args.variants.split(",") if s and s != args.storage]
+    for v in vlist:
         r = run_gpu(args, w, v, rank, world, dist)
-        variants[v] = variant_line(args, w, v, r)
+        variants[v] = variant_line(args, w, v, r, base_glups)
+    if not args.no_batched and world == 1:
+        variants["batched"] = run_batched(args)
+        variants["batched"]["speedup_vs_fp32"] = variants["batched"]["value"] / base_glups
+    errs = None
+    if rank == 0 and not args.no_oracle_error:
+        errs, err_case = oracle_errors(w, [args.storage] + vlist)
+        for v in vlist:
+            variants[v]["oracle_err"] = errs[v]
     e2e = None if args.no_e2e else run_e2e(args, w, args.storage)
     if dist is not None:
         dist.barrier()
@@ -333,6 +433,7 @@ def main():
         "dtype": "f32" if args.storage == "fp32" else "f32 (" + args.storage + " storage)",
         "data": "synthetic",
         "config": {"workload": describe(w), "nodes_per_gpu": w.nodes, "storage": args.storage,
+                   "tile": res["shape"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": f"state {bpn * w.nodes / 1e9:.2f} GB (two buffers) > 126 MB L2: "
                          "inputs larger than L2, no flush"},
@@ -341,6 +442,7 @@ def main():
                      "note": f"{bpn} algorithmic bytes per node ({FIELDS} stored values read and "
                              f"written) x {w.nodes} nodes per launch / mean launch time; peak "
                              f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "oracle_err": None if errs is None else {"case": err_case, args.storage: errs[args.storage]},
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "variants": variants,

@@ -100,6 +100,8 @@ typedef struct {
     int32_t tile_z;         /* z extent of one thread block's slab; 0 = automatic */
     int32_t graph_steps;    /* steps per captured CUDA graph replayed by tslb_step; 0 = automatic,
                                1 = plain launches */
+    int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 30 x 14,
+                               30 x 22, 30 x 30 interior nodes); 0 = automatic */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
                                (blocking, so ordered with the legacy default stream) */
 } tslb_options;
@@ -172,6 +174,39 @@ TSLB_API const char* tslb_status_string(tslb_status s);
 /* Number of step-kernel launches issued by this context so far (each launch
  * is one time step over the whole grid). */
 TSLB_API int64_t tslb_kernel_launches(const tslb_ctx* ctx);
+
+/* ---- Batches of independent grids (one launch per time step for all). ----
+ *
+ * A batch context advances `count` independent grids (each with its own size,
+ * omega, sigma and faces; same options, FP32 storage) together: each time
+ * step is one persistent kernel launch whose blocks take the tiles of all
+ * grids from a device work counter, and tslb_step replays those launches
+ * from a captured CUDA graph.  tslb_step, tslb_get_time, tslb_autotune,
+ * tslb_synchronize and tslb_destroy take batch contexts; the single-grid
+ * tslb_set_state / tslb_get_moments / tslb_get_phi / tslb_sums act on grid 0.
+ * Setting any grid's state restarts the step index of the batch at 0.
+ * Checkpoints (tslb_get_state / tslb_put_state) are single-grid only. */
+TSLB_API size_t tslb_batch_workspace_bytes(int32_t count, const tslb_grid* grids, const tslb_options* opt);
+TSLB_API tslb_status tslb_init_batch(tslb_ctx** out, int32_t count, const tslb_grid* grids,
+                                     tslb_lattice lattice, const double* omega, const double* sigma,
+                                     const tslb_boundary* bcs /* count entries, NULL = all periodic */,
+                                     const tslb_options* opt, void* workspace, size_t workspace_bytes);
+TSLB_API tslb_status tslb_batch_set_state(tslb_ctx* ctx, int32_t instance, const float* rho, const float* u,
+                                          const float* pi, const float* phi, int on_device);
+TSLB_API tslb_status tslb_batch_get_moments(tslb_ctx* ctx, int32_t instance, float* rho, float* u, float* pi,
+                                            int on_device);
+TSLB_API tslb_status tslb_batch_get_phi(tslb_ctx* ctx, int32_t instance, float* phi, int on_device);
+TSLB_API tslb_status tslb_batch_sums(tslb_ctx* ctx, int32_t instance, double* mass, double* phi_total);
+TSLB_API int32_t tslb_batch_count(const tslb_ctx* ctx);
+
+/* Tile-shape autotuner: times the step kernel for blocks of 8 and 12 warps
+ * and z slabs of 16, 24, 32, 48 and 64 planes (steps_per_trial launches
+ * each, CUDA events on the context stream) and keeps the fastest for all
+ * later steps.  Every trial recomputes the step from the current state into
+ * the spare buffer, so the state and the step index do not change.  Drops
+ * captured graphs; synchronises.  Reports the choice in *block_warps and
+ * *tile_z (either may be NULL). */
+TSLB_API tslb_status tslb_autotune(tslb_ctx* ctx, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z);
 
 /* The paper has no counterpart to this entry point; it serves callers that
  * must not allocate device memory when they ask for the totals.  cudaMalloc

@@ -26,7 +26,10 @@ __all__ = [
     "tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_set_state", "tslb_step",
     "tslb_get_moments", "tslb_get_phi", "tslb_sums", "tslb_get_time", "tslb_state_bytes",
     "tslb_get_state", "tslb_put_state", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
-    "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc", "Simulation", "SYMBOLS",
+    "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
+    "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
+    "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
+    "Simulation", "BatchSimulation", "SYMBOLS",
 ]
 
 TSLB_OK, TSLB_ERR_INVALID_ARG, TSLB_ERR_OOM, TSLB_ERR_CUDA, TSLB_ERR_UNSTABLE, TSLB_ERR_TIMEOUT, \
@@ -38,7 +41,9 @@ FACES = {"periodic": 0, "inlet": 1, "outflow": 2, "free_slip": 3}
 SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_set_state", "tslb_step",
            "tslb_get_moments", "tslb_get_phi", "tslb_sums", "tslb_get_time", "tslb_state_bytes",
            "tslb_get_state", "tslb_put_state", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
-           "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc")
+           "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
+           "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
+           "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune")
 
 
 class Grid(ctypes.Structure):
@@ -55,7 +60,8 @@ class Options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("interface_width", ctypes.c_float),
                 ("normal_eps", ctypes.c_float), ("field_scale", ctypes.c_float * 4),
                 ("check_every", ctypes.c_int32), ("tile_z", ctypes.c_int32),
-                ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("graph_steps", ctypes.c_int32), ("block_warps", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class TslbError(RuntimeError):
@@ -106,6 +112,20 @@ def lib() -> ctypes.CDLL:
             L.tslb_kernel_launches.restype = ctypes.c_int64
             L.tslb_field_sums_noalloc.argtypes = [VP, VP, ctypes.c_int64, VP, VP]
             L.tslb_field_sums_noalloc.restype = ctypes.c_int
+            L.tslb_batch_workspace_bytes.argtypes = [ctypes.c_int32, P(Grid), P(Options)]
+            L.tslb_batch_workspace_bytes.restype = ctypes.c_size_t
+            L.tslb_init_batch.argtypes = [P(VP), ctypes.c_int32, P(Grid), ctypes.c_int, P(ctypes.c_double),
+                                          P(ctypes.c_double), P(Boundary), P(Options), VP, ctypes.c_size_t]
+            L.tslb_batch_set_state.argtypes = [VP, ctypes.c_int32, VP, VP, VP, VP, ctypes.c_int]
+            L.tslb_batch_get_moments.argtypes = [VP, ctypes.c_int32, VP, VP, VP, ctypes.c_int]
+            L.tslb_batch_get_phi.argtypes = [VP, ctypes.c_int32, VP, ctypes.c_int]
+            L.tslb_batch_sums.argtypes = [VP, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double)]
+            L.tslb_batch_count.argtypes = [VP]
+            L.tslb_batch_count.restype = ctypes.c_int32
+            L.tslb_autotune.argtypes = [VP, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]
+            for name in ("tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments", "tslb_batch_get_phi",
+                         "tslb_batch_sums", "tslb_autotune"):
+                getattr(L, name).restype = ctypes.c_int
             for name in ("tslb_init", "tslb_set_state", "tslb_step", "tslb_get_moments", "tslb_get_phi",
                          "tslb_sums", "tslb_get_time", "tslb_get_state", "tslb_put_state",
                          "tslb_synchronize", "tslb_destroy"):
@@ -210,6 +230,54 @@ def tslb_field_sums_noalloc(rho: int, phi: int, n: int, out: int, stream: int = 
     _check(lib().tslb_field_sums_noalloc(rho, phi, int(n), out, stream or None), None)
 
 
+def tslb_batch_workspace_bytes(grids, opt: Optional[Options] = None) -> int:
+    arr = (Grid * len(grids))(*grids)
+    return int(lib().tslb_batch_workspace_bytes(len(grids), arr, ctypes.byref(opt) if opt else None))
+
+
+def tslb_init_batch(grids, omegas, sigmas, bcs=None, opt: Optional[Options] = None, workspace: int = 0,
+                    workspace_bytes: int = 0) -> int:
+    n = len(grids)
+    ctx = ctypes.c_void_p()
+    g = (Grid * n)(*grids)
+    om = (ctypes.c_double * n)(*[float(x) for x in omegas])
+    sg = (ctypes.c_double * n)(*[float(x) for x in sigmas])
+    b = (Boundary * n)(*bcs) if bcs is not None else None
+    st = lib().tslb_init_batch(ctypes.byref(ctx), n, g, TSLB_LATTICE_D3Q27_D3Q7, om, sg, b,
+                               ctypes.byref(opt) if opt else None, ctypes.c_void_p(workspace or None),
+                               ctypes.c_size_t(workspace_bytes))
+    _check(st, None)
+    return ctx.value
+
+
+def tslb_batch_set_state(ctx: int, i: int, rho: int, u: int, pi: int, phi: int, on_device: int):
+    _check(lib().tslb_batch_set_state(ctx, int(i), rho, u, pi or None, phi, int(on_device)), ctx)
+
+
+def tslb_batch_get_moments(ctx: int, i: int, rho: int, u: int, pi: int, on_device: int):
+    _check(lib().tslb_batch_get_moments(ctx, int(i), rho or None, u or None, pi or None, int(on_device)), ctx)
+
+
+def tslb_batch_get_phi(ctx: int, i: int, phi: int, on_device: int):
+    _check(lib().tslb_batch_get_phi(ctx, int(i), phi, int(on_device)), ctx)
+
+
+def tslb_batch_sums(ctx: int, i: int):
+    m, p = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tslb_batch_sums(ctx, int(i), ctypes.byref(m), ctypes.byref(p)), ctx)
+    return m.value, p.value
+
+
+def tslb_batch_count(ctx: int) -> int:
+    return int(lib().tslb_batch_count(ctx))
+
+
+def tslb_autotune(ctx: int, steps_per_trial: int = 8):
+    nw, tz = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().tslb_autotune(ctx, int(steps_per_trial), ctypes.byref(nw), ctypes.byref(tz)), ctx)
+    return nw.value, tz.value
+
+
 # ------------------------------------------------------------ convenience
 
 def _boundary_from(workload) -> Boundary:
@@ -235,7 +303,7 @@ class Simulation:
     """
 
     def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
-                 graph_steps: int = 0, check_every: int = 0, field_scale=None):
+                 graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Simulation needs a CUDA device")
@@ -250,6 +318,7 @@ class Simulation:
         o.tile_z = int(tile_z)
         o.graph_steps = int(graph_steps)
         o.check_every = int(check_every)
+        o.block_warps = int(block_warps)
         if field_scale is not None:
             for g in range(4):
                 o.field_scale[g] = float(field_scale[g])
@@ -347,6 +416,102 @@ class Simulation:
 
     def put_state(self, buf):
         tslb_put_state(self.ctx, buf.data_ptr(), 1 if buf.is_cuda else 0)
+
+    def synchronize(self):
+        tslb_synchronize(self.ctx)
+
+    def autotune(self, steps_per_trial: int = 8):
+        """Pick the fastest block shape and slab depth; the state is unchanged."""
+        return tslb_autotune(self.ctx, steps_per_trial)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            tslb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSimulation:
+    """Many independent grids (a list of :class:`inputs.Workload`) advanced
+    together: one persistent launch per time step, graph-replayed."""
+
+    def __init__(self, workloads, stream=None, tile_z: int = 0, block_warps: int = 0, graph_steps: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("BatchSimulation needs a CUDA device")
+        self.workloads = list(workloads)
+        widths = {float(w.width) for w in self.workloads}
+        eps = {float(getattr(w, "normal_eps", 1e-2)) for w in self.workloads}
+        if len(widths) != 1 or len(eps) != 1:
+            raise ValueError("a batch shares the interface width and the normal regularisation")
+        self.grids = [Grid(w.nx, w.ny, w.nz) for w in self.workloads]
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        o = tslb_default_options()
+        o.interface_width = widths.pop()
+        o.normal_eps = eps.pop()
+        o.tile_z = int(tile_z)
+        o.block_warps = int(block_warps)
+        o.graph_steps = int(graph_steps)
+        o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self.options = o
+        nbytes = tslb_batch_workspace_bytes(self.grids, o)
+        if nbytes == 0:
+            raise TslbError(TSLB_ERR_INVALID_ARG, "invalid grids or options")
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self._ws.data_ptr()
+        off = (-base) % 256
+        self.ctx = tslb_init_batch(self.grids, [w.omega for w in self.workloads], [w.sigma for w in self.workloads],
+                                   [_boundary_from(w) for w in self.workloads], o, base + off, nbytes)
+
+    @property
+    def nodes(self) -> int:
+        return sum(w.nodes for w in self.workloads)
+
+    def set_state(self, i: int, rho, u, phi, pi=None):
+        import torch
+        n = self.workloads[i].nodes
+        prep = lambda a, k: None if a is None else torch.as_tensor(a).to("cuda", torch.float32).contiguous().reshape(-1)
+        r, uu, ph, pp = prep(rho, n), prep(u, 3 * n), prep(phi, n), prep(pi, 6 * n)
+        torch.cuda.current_stream().synchronize()
+        tslb_batch_set_state(self.ctx, i, r.data_ptr(), uu.data_ptr(), pp.data_ptr() if pp is not None else 0,
+                             ph.data_ptr(), 1)
+        self.stream.synchronize()
+
+    def step(self, n: int = 1):
+        tslb_step(self.ctx, n)
+
+    def autotune(self, steps_per_trial: int = 4):
+        return tslb_autotune(self.ctx, steps_per_trial)
+
+    def fields_numpy(self, i: int):
+        import torch
+        w = self.workloads[i]
+        n = w.nodes
+        rho = torch.empty(n, dtype=torch.float32, device="cuda")
+        u = torch.empty(3 * n, dtype=torch.float32, device="cuda")
+        pi = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+        phi = torch.empty(n, dtype=torch.float32, device="cuda")
+        tslb_batch_get_moments(self.ctx, i, rho.data_ptr(), u.data_ptr(), pi.data_ptr(), 1)
+        tslb_batch_get_phi(self.ctx, i, phi.data_ptr(), 1)
+        s = (w.nz, w.ny, w.nx)
+        f = lambda t, lead: t.double().cpu().numpy().reshape(lead + s)
+        return f(rho, ()), f(u, (3,)), f(pi, (6,)), f(phi, ())
+
+    def sums(self, i: int):
+        return tslb_batch_sums(self.ctx, i)
+
+    @property
+    def t(self) -> int:
+        return tslb_get_time(self.ctx)
+
+    @property
+    def kernel_launches(self) -> int:
+        return tslb_kernel_launches(self.ctx)
 
     def synchronize(self):
         tslb_synchronize(self.ctx)

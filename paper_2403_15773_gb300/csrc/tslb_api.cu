@@ -1,40 +1,60 @@
-// Host side of the C ABI declared in include/tslb.h: contexts, argument
-// checking, workspace layout, state I/O, graph-captured time stepping, FP64
-// sums and checkpoints.  All compute runs in the kernels of tslb_step.cu.
+// Host side of the C ABI declared in include/tslb.h: contexts (one grid or a
+// batch of independent grids), argument checking, workspace layout, state
+// I/O, graph-captured time stepping, FP64 sums, checkpoints and the tile-shape
+// autotuner.  All compute runs in the kernels of tslb_step.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "tslb.h"
 #include "tslb_internal.h"
 
 using tslb::StepParams;
 
-struct tslb_ctx {
+namespace {
+
+// One grid of a context: its parameters, node count and its two state buffers.
+struct Instance {
     StepParams p;
+    long long N = 0;
+    void* buf[2] = {nullptr, nullptr};
+    int tile_begin = 0, tile_end = 0;  // batch: its tiles in the tile list
+    bool set = false;
+};
+
+}  // namespace
+
+struct tslb_ctx {
     int storage = 0;
     size_t elem = 4;
     int device = 0;
-    long long N = 0;
+    int sms = 1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool own_ws = false;
-    void* buf[2] = {nullptr, nullptr};
+    std::vector<Instance> inst;
+    bool batch = false;
+    int batch_nw = 8;
     float* staging = nullptr;
-    double* partials = nullptr;
+    double* partials = nullptr;   // step partials; state-sum partials after max_tiles
+    int max_tiles = 0;
     double* result = nullptr;
     long long* tdev = nullptr;
+    int* counters = nullptr;
+    tslb::BatchInstance* dinst = nullptr;
+    int4* dtiles = nullptr;
+    int ntiles = 0;
     int cur = 0;
     int64_t t = 0;
-    bool have_state = false;
-    int nparts = 0;
-    bool parts_valid = false;
+    bool parts_valid = false;  // step partials describe the current state
     int graph_steps = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int check_every = 0;
@@ -49,30 +69,12 @@ thread_local std::string g_init_err;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-struct Layout {
-    size_t state, staging, partials, result, tdev, total;
-};
-
-Layout layout_for(const StepParams& p, size_t elem, int storage) {
-    Layout L;
-    const size_t fs = (size_t)p.fstride;
-    L.state = 0;
-    size_t off = align256(tslb::NFIELDS * fs * elem) * 2;
-    L.staging = off;
-    off += align256(fs * sizeof(float));
-    L.partials = off;
-    off += align256((size_t)tslb::max_partials(p, storage) * 2 * sizeof(double));
-    L.result = off;
-    off += 256;
-    L.tdev = off;
-    off += 256;
-    L.total = off;
-    return L;
-}
-
 size_t elem_size(int storage) { return storage == TSLB_FP32 ? 4 : 2; }
 
 int auto_tile_z(int nz) { return nz < 32 ? nz : 32; }
+
+constexpr int kAutotuneTileZ[] = {16, 24, 32, 48, 64};
+constexpr int kMinTileZ = 16;  // smallest slab the batch tile list is sized for
 
 bool valid_grid(const tslb_grid* g, const int face[6], std::string& why) {
     const int n[3] = {g->nx, g->ny, g->nz};
@@ -142,6 +144,10 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
         why = "tile_z must be >= 0";
         return false;
     }
+    if (opt->block_warps != 0 && opt->block_warps != 8 && opt->block_warps != 12 && opt->block_warps != 16) {
+        why = "block_warps must be 0, 8, 12 or 16";
+        return false;
+    }
     if (b.face[4] == TSLB_BC_INLET && !(b.inlet_diameter >= 0.f)) {
         why = "inlet_diameter must be >= 0";
         return false;
@@ -152,6 +158,7 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     p.nz = grid->nz;
     for (int k = 0; k < 6; ++k) p.face[k] = b.face[k];
     p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz) : auto_tile_z(grid->nz);
+    p.block_warps = opt->block_warps > 0 ? opt->block_warps : 12;
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     p.fstride = (N + 63) / 64 * 64;
     p.omega = (float)omega;
@@ -189,9 +196,9 @@ tslb_status cuda_fail(tslb_ctx* c, cudaError_t e, const char* what) {
     return TSLB_ERR_CUDA;
 }
 
-#define CK(call, what)                                      \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
+#define CK(call, what)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
@@ -210,24 +217,125 @@ bool is_device_ptr(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-tslb_status put_field(tslb_ctx* c, const float* src, int field, int on_device) {
+// Tiles of one grid for a block of `nw` warps and slabs of `tile_z` planes.
+int tiles_of(const StepParams& p, int nw, int tile_z) {
+    StepParams q = p;
+    q.block_warps = nw;
+    q.tile_z = std::min(tile_z, p.nz);
+    const tslb::LaunchShape sh = tslb::step_shape(q, 0);
+    return (int)(sh.grid.x * sh.grid.y * sh.grid.z);
+}
+
+// Workspace layout.  Per grid: two state buffers.  Shared: one staging field
+// for host I/O, FP64 partials (step tiles, then state-sum blocks), the result
+// pair, the two-slot step counter, the two batch tile counters, and for a
+// batch the device copy of the instances and the tile list.
+struct Layout {
+    std::vector<size_t> state;
+    size_t staging, partials, result, tdev, counters, dinst, dtiles, total;
+    int max_tiles, max_conv;
+};
+
+Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, bool batch) {
+    Layout L;
+    size_t off = 0;
+    long long maxf = 0;
+    int tiles = 0, conv = 0;
+    for (const StepParams& p : ps) {
+        L.state.push_back(off);
+        off += 2 * align256(tslb::NFIELDS * (size_t)p.fstride * elem);
+        maxf = std::max(maxf, p.fstride);
+        if (batch)
+            tiles += tiles_of(p, 8, std::min(p.tile_z, kMinTileZ));
+        else
+            tiles = std::max(tiles, tslb::max_partials(p, storage));
+        conv = std::max(conv, tslb::max_partials(p, storage));
+    }
+    L.max_tiles = tiles;
+    L.max_conv = conv;
+    L.staging = off;
+    off += align256((size_t)maxf * sizeof(float));
+    L.partials = off;
+    off += align256((size_t)(tiles + conv) * 2 * sizeof(double));
+    L.result = off;
+    off += 256;
+    L.tdev = off;
+    off += 256;
+    L.counters = off;
+    off += 256;
+    L.dinst = off;
+    off += batch ? align256(ps.size() * sizeof(tslb::BatchInstance)) : 0;
+    L.dtiles = off;
+    off += batch ? align256((size_t)tiles * sizeof(int4)) : 0;
+    L.total = off;
+    return L;
+}
+
+tslb_status put_field(tslb_ctx* c, Instance& I, const float* src, int field, int on_device) {
     const float* dsrc = src;
     if (!on_device) {
-        CK(cudaMemcpyAsync(c->staging, src, (size_t)c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+        CK(cudaMemcpyAsync(c->staging, src, (size_t)I.N * sizeof(float), cudaMemcpyHostToDevice, c->stream),
            "host-to-device copy");
         dsrc = c->staging;
     }
-    CK(tslb::launch_put_field(c->p, c->storage, dsrc, field, c->buf[c->cur], c->stream), "field conversion");
+    CK(tslb::launch_put_field(I.p, c->storage, dsrc, field, I.buf[c->cur], c->stream), "field conversion");
     return TSLB_OK;
 }
 
-tslb_status get_field(tslb_ctx* c, float* dst, int field, int on_device) {
+tslb_status get_field(tslb_ctx* c, Instance& I, float* dst, int field, int on_device) {
     float* ddst = on_device ? dst : c->staging;
-    CK(tslb::launch_get_field(c->p, c->storage, c->buf[c->cur], field, ddst, c->stream), "field conversion");
+    CK(tslb::launch_get_field(I.p, c->storage, I.buf[c->cur], field, ddst, c->stream), "field conversion");
     if (!on_device)
-        CK(cudaMemcpyAsync(dst, c->staging, (size_t)c->N * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+        CK(cudaMemcpyAsync(dst, c->staging, (size_t)I.N * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
            "device-to-host copy");
     return TSLB_OK;
+}
+
+// Builds the batch tile list for the current block shape and slab depth and
+// uploads it with the instances (synchronous: pageable host memory).
+tslb_status upload_batch(tslb_ctx* c) {
+    std::vector<int4> tiles;
+    std::vector<tslb::BatchInstance> di(c->inst.size());
+    for (size_t i = 0; i < c->inst.size(); ++i) {
+        Instance& I = c->inst[i];
+        I.p.block_warps = c->batch_nw;
+        const tslb::LaunchShape sh = tslb::step_shape(I.p, c->storage);
+        I.tile_begin = (int)tiles.size();
+        for (unsigned bz = 0; bz < sh.grid.z; ++bz)
+            for (unsigned by = 0; by < sh.grid.y; ++by)
+                for (unsigned bx = 0; bx < sh.grid.x; ++bx) tiles.push_back(make_int4((int)i, bx, by, bz));
+        I.tile_end = (int)tiles.size();
+        di[i].p = I.p;
+        di[i].buf[0] = I.buf[0];
+        di[i].buf[1] = I.buf[1];
+    }
+    if ((int)tiles.size() > c->max_tiles) return bad(c, "batch tile list exceeds its workspace");
+    c->ntiles = (int)tiles.size();
+    CK(cudaMemcpyAsync(c->dinst, di.data(), di.size() * sizeof(di[0]), cudaMemcpyHostToDevice, c->stream),
+       "batch instances upload");
+    CK(cudaMemcpyAsync(c->dtiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream),
+       "batch tiles upload");
+    CK(cudaStreamSynchronize(c->stream), "batch upload synchronise");
+    return TSLB_OK;
+}
+
+// One time step from parity q (state buf[q], step counter tdev[q]) to q ^ 1.
+cudaError_t launch_one(tslb_ctx* c, int q) {
+    if (!c->batch) {
+        Instance& I = c->inst[0];
+        return tslb::launch_step(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
+                                 c->partials, c->stream);
+    }
+    return tslb::launch_batch_step(c->batch_nw, c->dinst, c->dtiles, c->ntiles, q, c->tdev + q, c->tdev + (q ^ 1),
+                                   c->counters, c->partials, c->sms, c->stream);
+}
+
+void drop_graphs(tslb_ctx* c) {
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k]) {
+            cudaGraphExecDestroy(c->graph[k]);
+            c->graph[k] = nullptr;
+        }
 }
 
 tslb_status capture_graph(tslb_ctx* c, int parity) {
@@ -236,8 +344,7 @@ tslb_status capture_graph(tslb_ctx* c, int parity) {
     int q = parity;
     cudaError_t le = cudaSuccess;
     for (int k = 0; k < c->graph_steps && le == cudaSuccess; ++k) {
-        le = tslb::launch_step(c->p, c->storage, c->buf[q], c->buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
-                               c->partials, c->stream);
+        le = launch_one(c, q);
         q ^= 1;
     }
     cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
@@ -255,58 +362,44 @@ tslb_status capture_graph(tslb_ctx* c, int parity) {
     return TSLB_OK;
 }
 
-tslb_status finish_sums(tslb_ctx* c, double* mass, double* phi_total) {
-    if (!c->parts_valid) {
-        CK(tslb::launch_state_sums(c->p, c->storage, c->buf[c->cur], c->partials, &c->nparts, c->stream),
-           "state sums");
-        c->parts_valid = true;
+// FP64 totals of one grid: from the step partials when they describe the
+// current state, else from a reduction of the stored fields.
+tslb_status finish_sums(tslb_ctx* c, int i, double* mass, double* phi_total) {
+    Instance& I = c->inst[i];
+    const double* parts = c->partials;
+    int n = 0;
+    if (c->parts_valid) {
+        if (c->batch) {
+            parts = c->partials + 2 * (size_t)I.tile_begin;
+            n = I.tile_end - I.tile_begin;
+        } else {
+            n = tiles_of(I.p, I.p.block_warps, I.p.tile_z);
+        }
+    } else {
+        double* sp = c->partials + 2 * (size_t)c->max_tiles;
+        CK(tslb::launch_state_sums(I.p, c->storage, I.buf[c->cur], sp, &n, c->stream), "state sums");
+        parts = sp;
     }
-    CK(tslb::launch_finish_sums(c->partials, c->nparts, c->result, c->stream), "sum reduction");
+    CK(tslb::launch_finish_sums(parts, n, c->result, c->stream), "sum reduction");
     double r[2];
     CK(cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream), "sums copy");
     CK(cudaStreamSynchronize(c->stream), "sums synchronise");
-    *mass = (double)c->N + r[0];
+    *mass = (double)I.N + r[0];
     *phi_total = r[1];
     if (!std::isfinite(*mass) || !std::isfinite(*phi_total))
         return bad(c, "total mass or phase field is not finite", TSLB_ERR_UNSTABLE);
     return TSLB_OK;
 }
 
-}  // namespace
-
-namespace tslb {
-void set_global_error(const char* msg) { g_init_err = msg ? msg : ""; }
-}  // namespace tslb
-
-extern "C" {
-
-void tslb_default_options(tslb_options* opt) {
-    if (!opt) return;
-    std::memset(opt, 0, sizeof(*opt));
-    opt->storage = TSLB_FP32;
-    opt->interface_width = 3.f;
-    opt->normal_eps = 1e-2f;
-    opt->check_every = 0;
-    opt->tile_z = 0;
-    opt->graph_steps = 0;
-    opt->cuda_stream = nullptr;
+tslb_status check_instance(tslb_ctx* c, int i) {
+    if (i < 0 || i >= (int)c->inst.size()) return bad(c, "instance index out of range");
+    return TSLB_OK;
 }
 
-size_t tslb_workspace_bytes(const tslb_grid* grid, const tslb_options* opt) {
-    tslb_options o;
-    tslb_default_options(&o);
-    if (opt) o = *opt;
-    tslb_boundary b;
-    std::memset(&b, 0, sizeof(b));
-    StepParams p;
-    std::string why;
-    // the face rules only affect validity, not the size: check with periodic faces
-    if (!make_params(grid, 1.0, 0.0, &b, &o, p, why)) return 0;
-    return layout_for(p, elem_size(o.storage), o.storage).total;
-}
-
-tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattice, double omega, double sigma,
-                      const tslb_boundary* bc, const tslb_options* opt, void* workspace, size_t workspace_bytes) {
+// Creates a context for `count` grids (count == 1: one grid, no batch).
+tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_lattice lattice, const double* omega,
+                   const double* sigma, const tslb_boundary* bcs, const tslb_options* opt, void* workspace,
+                   size_t workspace_bytes, bool batch) {
     if (!out) {
         g_init_err = "out is NULL";
         return TSLB_ERR_INVALID_ARG;
@@ -316,39 +409,55 @@ tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattic
         g_init_err = "unknown lattice";
         return TSLB_ERR_INVALID_ARG;
     }
+    if (count < 1 || !grids || !omega || !sigma) {
+        g_init_err = "count >= 1 and grids, omega, sigma are required";
+        return TSLB_ERR_INVALID_ARG;
+    }
     tslb_options o;
     tslb_default_options(&o);
     if (opt) o = *opt;
-    StepParams p;
-    std::string why;
-    if (!make_params(grid, omega, sigma, bc, &o, p, why)) {
-        g_init_err = why;
+    if (batch && o.storage != TSLB_FP32) {
+        g_init_err = "batches use FP32 storage";
         return TSLB_ERR_INVALID_ARG;
+    }
+    if (batch && o.block_warps != 0 && o.block_warps != 8 && o.block_warps != 12) {
+        g_init_err = "batches use blocks of 8 or 12 warps";
+        return TSLB_ERR_INVALID_ARG;
+    }
+    std::vector<StepParams> ps(count);
+    for (int i = 0; i < count; ++i) {
+        std::string why;
+        if (!make_params(&grids[i], omega[i], sigma[i], bcs ? &bcs[i] : nullptr, &o, ps[i], why)) {
+            g_init_err = count > 1 ? "grid " + std::to_string(i) + ": " + why : why;
+            return TSLB_ERR_INVALID_ARG;
+        }
+        if (batch) ps[i].tile_z = o.tile_z > 0 ? std::min(o.tile_z, grids[i].nz) : std::min(32, grids[i].nz);
     }
     tslb_ctx* c = new (std::nothrow) tslb_ctx();
     if (!c) {
         g_init_err = "host allocation failed";
         return TSLB_ERR_OOM;
     }
-    c->p = p;
     c->storage = o.storage;
     c->elem = elem_size(o.storage);
-    c->N = (long long)grid->nx * grid->ny * grid->nz;
+    c->batch = batch;
+    c->batch_nw = o.block_warps > 0 ? o.block_warps : 8;
     c->check_every = o.check_every > 0 ? o.check_every : 0;
     int gs = o.graph_steps > 0 ? o.graph_steps : 16;
     c->graph_steps = gs >= 2 ? gs & ~1 : 1;
-    tslb_status st = TSLB_OK;
     auto fail = [&](tslb_status s) {
         g_init_err = c->err;
         tslb_destroy(c);
         return s;
     };
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {
         c->err = std::string("no CUDA device: ") + cudaGetErrorString(e);
         return fail(TSLB_ERR_CUDA);
     }
     e = tslb::prepare_kernels(c->storage);
+    if (e == cudaSuccess && batch) e = tslb::prepare_batch_kernels();
     if (e != cudaSuccess) {
         c->err = std::string("kernel set-up: ") + cudaGetErrorString(e);
         return fail(TSLB_ERR_CUDA);
@@ -363,10 +472,10 @@ tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattic
         }
         c->own_stream = true;
     }
-    const Layout L = layout_for(p, c->elem, c->storage);
+    const Layout L = layout_for(ps, c->elem, c->storage, batch);
     if (workspace) {
         if (workspace_bytes < L.total) {
-            c->err = "workspace smaller than tslb_workspace_bytes()";
+            c->err = "workspace smaller than the workspace-bytes query";
             return fail(TSLB_ERR_OOM);
         }
         if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) {
@@ -387,54 +496,175 @@ tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattic
         c->ws_bytes = L.total;
     }
     char* base = static_cast<char*>(c->ws);
-    c->buf[0] = base + L.state;
-    c->buf[1] = base + L.state + align256(tslb::NFIELDS * (size_t)p.fstride * c->elem);
+    c->inst.resize(count);
+    for (int i = 0; i < count; ++i) {
+        Instance& I = c->inst[i];
+        I.p = ps[i];
+        I.N = (long long)grids[i].nx * grids[i].ny * grids[i].nz;
+        I.buf[0] = base + L.state[i];
+        I.buf[1] = base + L.state[i] + align256(tslb::NFIELDS * (size_t)ps[i].fstride * c->elem);
+    }
     c->staging = reinterpret_cast<float*>(base + L.staging);
     c->partials = reinterpret_cast<double*>(base + L.partials);
+    c->max_tiles = L.max_tiles;
     c->result = reinterpret_cast<double*>(base + L.result);
     c->tdev = reinterpret_cast<long long*>(base + L.tdev);
-    (void)st;
+    c->counters = reinterpret_cast<int*>(base + L.counters);
+    c->dinst = reinterpret_cast<tslb::BatchInstance*>(base + L.dinst);
+    c->dtiles = reinterpret_cast<int4*>(base + L.dtiles);
+    e = cudaMemsetAsync(c->counters, 0, 256, c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("counter reset: ") + cudaGetErrorString(e);
+        return fail(TSLB_ERR_CUDA);
+    }
+    if (batch) {
+        tslb_status s = upload_batch(c);
+        if (s != TSLB_OK) return fail(s);
+    }
     *out = c;
     return TSLB_OK;
 }
 
-tslb_status tslb_set_state(tslb_ctx* c, const float* rho, const float* u, const float* pi, const float* phi,
-                           int on_device) {
-    if (!c) return TSLB_ERR_INVALID_ARG;
+tslb_status set_state_of(tslb_ctx* c, int i, const float* rho, const float* u, const float* pi, const float* phi,
+                         int on_device) {
     if (!rho || !u || !phi) return bad(c, "rho, u and phi are required");
     if (on_device && (!is_device_ptr(rho) || !is_device_ptr(u) || !is_device_ptr(phi) ||
                       (pi && !is_device_ptr(pi))))
         return bad(c, "on_device pointers must be device memory");
     CK(cudaSetDevice(c->device), "set device");
-    c->cur = 0;
-    const long long N = c->N;
+    Instance& I = c->inst[i];
+    const long long N = I.N;
     tslb_status s;
-    if ((s = put_field(c, rho, tslb::F_DRHO, on_device)) != TSLB_OK) return s;
+    if ((s = put_field(c, I, rho, tslb::F_DRHO, on_device)) != TSLB_OK) return s;
     for (int a = 0; a < 3; ++a)
-        if ((s = put_field(c, u + a * N, tslb::F_UX + a, on_device)) != TSLB_OK) return s;
+        if ((s = put_field(c, I, u + a * N, tslb::F_UX + a, on_device)) != TSLB_OK) return s;
     if (pi) {
         for (int k = 0; k < 6; ++k)
-            if ((s = put_field(c, pi + k * N, tslb::F_PXX + k, on_device)) != TSLB_OK) return s;
+            if ((s = put_field(c, I, pi + k * N, tslb::F_PXX + k, on_device)) != TSLB_OK) return s;
     } else {
-        char* b0 = static_cast<char*>(c->buf[0]);
-        CK(cudaMemsetAsync(b0 + (size_t)tslb::F_PXX * c->p.fstride * c->elem, 0, 6 * (size_t)c->p.fstride * c->elem,
-                           c->stream),
+        char* b0 = static_cast<char*>(I.buf[c->cur]);
+        CK(cudaMemsetAsync(b0 + (size_t)tslb::F_PXX * I.p.fstride * c->elem, 0,
+                           6 * (size_t)I.p.fstride * c->elem, c->stream),
            "zero P");
     }
-    if ((s = put_field(c, phi, tslb::F_PHI, on_device)) != TSLB_OK) return s;
-    CK(cudaMemsetAsync(c->tdev, 0, 2 * sizeof(long long), c->stream), "step counter");
+    if ((s = put_field(c, I, phi, tslb::F_PHI, on_device)) != TSLB_OK) return s;
+    // the step index restarts with every state that is set
+    long long tt[2] = {0, 0};
+    CK(cudaMemcpyAsync(c->tdev, tt, sizeof(tt), cudaMemcpyHostToDevice, c->stream), "step counter");
     c->t = 0;
-    c->have_state = true;
+    I.set = true;
     c->parts_valid = false;
     c->since_check = 0;
-    if (!on_device) CK(cudaStreamSynchronize(c->stream), "set_state synchronise");  // staging reuse
+    CK(cudaStreamSynchronize(c->stream), "set_state synchronise");  // staging and tt reuse
     return TSLB_OK;
+}
+
+tslb_status get_moments_of(tslb_ctx* c, int i, float* rho, float* u, float* pi, int on_device) {
+    Instance& I = c->inst[i];
+    if (!I.set) return bad(c, "no state", TSLB_ERR_STATE);
+    if (on_device && ((rho && !is_device_ptr(rho)) || (u && !is_device_ptr(u)) || (pi && !is_device_ptr(pi))))
+        return bad(c, "on_device pointers must be device memory");
+    CK(cudaSetDevice(c->device), "set device");
+    const long long N = I.N;
+    tslb_status s;
+    if (rho && (s = get_field(c, I, rho, tslb::F_DRHO, on_device)) != TSLB_OK) return s;
+    for (int a = 0; u && a < 3; ++a)
+        if ((s = get_field(c, I, u + a * N, tslb::F_UX + a, on_device)) != TSLB_OK) return s;
+    for (int k = 0; pi && k < 6; ++k)
+        if ((s = get_field(c, I, pi + k * N, tslb::F_PXX + k, on_device)) != TSLB_OK) return s;
+    CK(cudaStreamSynchronize(c->stream), "get_moments synchronise");
+    return TSLB_OK;
+}
+
+tslb_status get_phi_of(tslb_ctx* c, int i, float* phi, int on_device) {
+    Instance& I = c->inst[i];
+    if (!I.set) return bad(c, "no state", TSLB_ERR_STATE);
+    if (!phi) return bad(c, "phi is NULL");
+    if (on_device && !is_device_ptr(phi)) return bad(c, "on_device pointers must be device memory");
+    CK(cudaSetDevice(c->device), "set device");
+    tslb_status s = get_field(c, I, phi, tslb::F_PHI, on_device);
+    if (s != TSLB_OK) return s;
+    CK(cudaStreamSynchronize(c->stream), "get_phi synchronise");
+    return TSLB_OK;
+}
+
+bool all_set(const tslb_ctx* c) {
+    for (const Instance& I : c->inst)
+        if (!I.set) return false;
+    return true;
+}
+
+}  // namespace
+
+namespace tslb {
+void set_global_error(const char* msg) { g_init_err = msg ? msg : ""; }
+}  // namespace tslb
+
+extern "C" {
+
+void tslb_default_options(tslb_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->storage = TSLB_FP32;
+    opt->interface_width = 3.f;
+    opt->normal_eps = 1e-2f;
+    opt->check_every = 0;
+    opt->tile_z = 0;
+    opt->graph_steps = 0;
+    opt->block_warps = 0;
+    opt->cuda_stream = nullptr;
+}
+
+size_t tslb_workspace_bytes(const tslb_grid* grid, const tslb_options* opt) {
+    return tslb_batch_workspace_bytes(1, grid, opt);
+}
+
+size_t tslb_batch_workspace_bytes(int32_t count, const tslb_grid* grids, const tslb_options* opt) {
+    if (count < 1 || !grids) return 0;
+    tslb_options o;
+    tslb_default_options(&o);
+    if (opt) o = *opt;
+    tslb_boundary b;
+    std::memset(&b, 0, sizeof(b));
+    std::vector<StepParams> ps(count);
+    for (int i = 0; i < count; ++i) {
+        std::string why;
+        // the face rules only affect validity, not the size: size with periodic faces
+        if (!make_params(&grids[i], 1.0, 0.0, &b, &o, ps[i], why)) return 0;
+    }
+    return layout_for(ps, elem_size(o.storage), o.storage, count > 1).total;
+}
+
+tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattice, double omega, double sigma,
+                      const tslb_boundary* bc, const tslb_options* opt, void* workspace, size_t workspace_bytes) {
+    return create(out, 1, grid, lattice, &omega, &sigma, bc, opt, workspace, workspace_bytes, false);
+}
+
+tslb_status tslb_init_batch(tslb_ctx** out, int32_t count, const tslb_grid* grids, tslb_lattice lattice,
+                            const double* omega, const double* sigma, const tslb_boundary* bcs,
+                            const tslb_options* opt, void* workspace, size_t workspace_bytes) {
+    return create(out, count, grids, lattice, omega, sigma, bcs, opt, workspace, workspace_bytes, count > 1);
+}
+
+tslb_status tslb_set_state(tslb_ctx* c, const float* rho, const float* u, const float* pi, const float* phi,
+                           int on_device) {
+    if (!c) return TSLB_ERR_INVALID_ARG;
+    c->cur = 0;
+    return set_state_of(c, 0, rho, u, pi, phi, on_device);
+}
+
+tslb_status tslb_batch_set_state(tslb_ctx* c, int32_t instance, const float* rho, const float* u, const float* pi,
+                                 const float* phi, int on_device) {
+    if (!c) return TSLB_ERR_INVALID_ARG;
+    tslb_status s = check_instance(c, instance);
+    if (s != TSLB_OK) return s;
+    return set_state_of(c, instance, rho, u, pi, phi, on_device);
 }
 
 tslb_status tslb_step(tslb_ctx* c, int64_t n) {
     if (!c) return TSLB_ERR_INVALID_ARG;
     if (n < 0) return bad(c, "n must be >= 0");
-    if (!c->have_state) return bad(c, "tslb_step before tslb_set_state", TSLB_ERR_STATE);
+    if (!all_set(c)) return bad(c, "tslb_step before the state of every grid is set", TSLB_ERR_STATE);
     CK(cudaSetDevice(c->device), "set device");
     while (n > 0) {
         int64_t chunk = n;
@@ -458,26 +688,23 @@ tslb_status tslb_step(tslb_ctx* c, int64_t n) {
             c->launches += c->graph_steps;
         }
         for (; done < chunk; ++done) {
-            const int q = c->cur;
-            CK(tslb::launch_step(c->p, c->storage, c->buf[q], c->buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
-                                 c->partials, c->stream),
-               "step launch");
+            CK(launch_one(c, c->cur), "step launch");
             c->cur ^= 1;
             c->launches += 1;
         }
         // graphs hold an even number of steps, so only plain launches flip cur
         c->t += chunk;
         n -= chunk;
-        const tslb::LaunchShape sh = tslb::step_shape(c->p, c->storage);
-        c->nparts = (int)(sh.grid.x * sh.grid.y * sh.grid.z);
         c->parts_valid = true;
         if (c->check_every > 0) {
             c->since_check += chunk;
             if (c->since_check >= c->check_every) {
                 c->since_check = 0;
-                double m, ph;
-                tslb_status s = finish_sums(c, &m, &ph);
-                if (s != TSLB_OK) return s;
+                for (int i = 0; i < (int)c->inst.size(); ++i) {
+                    double m, ph;
+                    tslb_status s = finish_sums(c, i, &m, &ph);
+                    if (s != TSLB_OK) return s;
+                }
             }
         }
     }
@@ -486,39 +713,41 @@ tslb_status tslb_step(tslb_ctx* c, int64_t n) {
 
 tslb_status tslb_get_moments(tslb_ctx* c, float* rho, float* u, float* pi, int on_device) {
     if (!c) return TSLB_ERR_INVALID_ARG;
-    if (!c->have_state) return bad(c, "no state", TSLB_ERR_STATE);
-    if (on_device && ((rho && !is_device_ptr(rho)) || (u && !is_device_ptr(u)) || (pi && !is_device_ptr(pi))))
-        return bad(c, "on_device pointers must be device memory");
-    CK(cudaSetDevice(c->device), "set device");
-    const long long N = c->N;
-    tslb_status s;
-    if (rho && (s = get_field(c, rho, tslb::F_DRHO, on_device)) != TSLB_OK) return s;
-    for (int a = 0; u && a < 3; ++a)
-        if ((s = get_field(c, u + a * N, tslb::F_UX + a, on_device)) != TSLB_OK) return s;
-    for (int k = 0; pi && k < 6; ++k)
-        if ((s = get_field(c, pi + k * N, tslb::F_PXX + k, on_device)) != TSLB_OK) return s;
-    CK(cudaStreamSynchronize(c->stream), "get_moments synchronise");
-    return TSLB_OK;
+    return get_moments_of(c, 0, rho, u, pi, on_device);
+}
+
+tslb_status tslb_batch_get_moments(tslb_ctx* c, int32_t instance, float* rho, float* u, float* pi,
+                                   int on_device) {
+    if (!c) return TSLB_ERR_INVALID_ARG;
+    tslb_status s = check_instance(c, instance);
+    if (s != TSLB_OK) return s;
+    return get_moments_of(c, instance, rho, u, pi, on_device);
 }
 
 tslb_status tslb_get_phi(tslb_ctx* c, float* phi, int on_device) {
     if (!c) return TSLB_ERR_INVALID_ARG;
-    if (!c->have_state) return bad(c, "no state", TSLB_ERR_STATE);
-    if (!phi) return bad(c, "phi is NULL");
-    if (on_device && !is_device_ptr(phi)) return bad(c, "on_device pointers must be device memory");
-    CK(cudaSetDevice(c->device), "set device");
-    tslb_status s = get_field(c, phi, tslb::F_PHI, on_device);
+    return get_phi_of(c, 0, phi, on_device);
+}
+
+tslb_status tslb_batch_get_phi(tslb_ctx* c, int32_t instance, float* phi, int on_device) {
+    if (!c) return TSLB_ERR_INVALID_ARG;
+    tslb_status s = check_instance(c, instance);
     if (s != TSLB_OK) return s;
-    CK(cudaStreamSynchronize(c->stream), "get_phi synchronise");
-    return TSLB_OK;
+    return get_phi_of(c, instance, phi, on_device);
 }
 
 tslb_status tslb_sums(tslb_ctx* c, double* mass, double* phi_total) {
+    return tslb_batch_sums(c, 0, mass, phi_total);
+}
+
+tslb_status tslb_batch_sums(tslb_ctx* c, int32_t instance, double* mass, double* phi_total) {
     if (!c) return TSLB_ERR_INVALID_ARG;
     if (!mass || !phi_total) return bad(c, "mass and phi_total are required");
-    if (!c->have_state) return bad(c, "no state", TSLB_ERR_STATE);
+    tslb_status s = check_instance(c, instance);
+    if (s != TSLB_OK) return s;
+    if (!c->inst[instance].set) return bad(c, "no state", TSLB_ERR_STATE);
     CK(cudaSetDevice(c->device), "set device");
-    return finish_sums(c, mass, phi_total);
+    return finish_sums(c, instance, mass, phi_total);
 }
 
 tslb_status tslb_get_time(const tslb_ctx* c, int64_t* t) {
@@ -527,21 +756,93 @@ tslb_status tslb_get_time(const tslb_ctx* c, int64_t* t) {
     return TSLB_OK;
 }
 
+tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z) {
+    if (!c) return TSLB_ERR_INVALID_ARG;
+    if (steps_per_trial < 1) return bad(c, "steps_per_trial must be >= 1");
+    if (!all_set(c)) return bad(c, "tslb_autotune before the state of every grid is set", TSLB_ERR_STATE);
+    CK(cudaSetDevice(c->device), "set device");
+    const int q = c->cur;
+    const int warps_single[] = {8, 12};
+    const int warps_batch[] = {8, 12};
+    const int* warps = c->batch ? warps_batch : warps_single;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event create");
+    CK(cudaEventCreate(&e1), "event create");
+    std::vector<int> keep_tz(c->inst.size());
+    for (size_t i = 0; i < c->inst.size(); ++i) keep_tz[i] = c->inst[i].p.tile_z;
+    float best = 1e30f;
+    int best_nw = c->batch ? c->batch_nw : c->inst[0].p.block_warps, best_tz = keep_tz[0];
+    tslb_status st = TSLB_OK;
+    for (int wi = 0; wi < 2 && st == TSLB_OK; ++wi)
+        for (int tz : kAutotuneTileZ) {
+            // each trial re-runs the step from the current state into the other
+            // buffer, so the state itself does not advance
+            for (Instance& I : c->inst) {
+                I.p.block_warps = warps[wi];
+                I.p.tile_z = std::min(tz, I.p.nz);
+            }
+            if (c->batch) {
+                c->batch_nw = warps[wi];
+                if ((st = upload_batch(c)) != TSLB_OK) break;
+            }
+            cudaError_t e = launch_one(c, q);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int k = 0; k < steps_per_trial && e == cudaSuccess; ++k) e = launch_one(c, q);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                st = cuda_fail(c, e, "autotune trial");
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_nw = warps[wi];
+                best_tz = tz;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // apply the winner (or restore on failure)
+    for (size_t i = 0; i < c->inst.size(); ++i) {
+        Instance& I = c->inst[i];
+        I.p.block_warps = best_nw;
+        I.p.tile_z = st == TSLB_OK ? std::min(best_tz, I.p.nz) : keep_tz[i];
+    }
+    if (c->batch) {
+        c->batch_nw = best_nw;
+        tslb_status s2 = upload_batch(c);
+        if (st == TSLB_OK) st = s2;
+    }
+    // the trials wrote the other buffer and the other step-counter slot: restore it
+    long long tt = (long long)c->t;
+    CK(cudaMemcpyAsync(c->tdev + (q ^ 1), &tt, sizeof(tt), cudaMemcpyHostToDevice, c->stream), "step counter");
+    CK(cudaStreamSynchronize(c->stream), "autotune synchronise");
+    drop_graphs(c);
+    c->parts_valid = false;
+    if (block_warps) *block_warps = best_nw;
+    if (tile_z) *tile_z = best_tz;
+    return st;
+}
+
 size_t tslb_state_bytes(const tslb_ctx* c) {
     if (!c) return 0;
-    return (size_t)tslb::NFIELDS * (size_t)c->N * c->elem + sizeof(int64_t);
+    return (size_t)tslb::NFIELDS * (size_t)c->inst[0].N * c->elem + sizeof(int64_t);
 }
 
 tslb_status tslb_get_state(tslb_ctx* c, void* dst, int on_device) {
     if (!c || !dst) return TSLB_ERR_INVALID_ARG;
-    if (!c->have_state) return bad(c, "no state", TSLB_ERR_STATE);
+    if (c->batch) return bad(c, "checkpoints are per single-grid context");
+    Instance& I = c->inst[0];
+    if (!I.set) return bad(c, "no state", TSLB_ERR_STATE);
     if (on_device && !is_device_ptr(dst)) return bad(c, "on_device pointers must be device memory");
     CK(cudaSetDevice(c->device), "set device");
-    const size_t fb = (size_t)c->N * c->elem;
+    const size_t fb = (size_t)I.N * c->elem;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     for (int f = 0; f < tslb::NFIELDS; ++f)
         CK(cudaMemcpyAsync(static_cast<char*>(dst) + f * fb,
-                           static_cast<const char*>(c->buf[c->cur]) + (size_t)f * c->p.fstride * c->elem, fb, kind,
+                           static_cast<const char*>(I.buf[c->cur]) + (size_t)f * I.p.fstride * c->elem, fb, kind,
                            c->stream),
            "state copy");
     int64_t t = c->t;
@@ -556,13 +857,15 @@ tslb_status tslb_get_state(tslb_ctx* c, void* dst, int on_device) {
 
 tslb_status tslb_put_state(tslb_ctx* c, const void* src, int on_device) {
     if (!c || !src) return TSLB_ERR_INVALID_ARG;
+    if (c->batch) return bad(c, "checkpoints are per single-grid context");
     if (on_device && !is_device_ptr(src)) return bad(c, "on_device pointers must be device memory");
     CK(cudaSetDevice(c->device), "set device");
-    const size_t fb = (size_t)c->N * c->elem;
+    Instance& I = c->inst[0];
+    const size_t fb = (size_t)I.N * c->elem;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     c->cur = 0;
     for (int f = 0; f < tslb::NFIELDS; ++f)
-        CK(cudaMemcpyAsync(static_cast<char*>(c->buf[0]) + (size_t)f * c->p.fstride * c->elem,
+        CK(cudaMemcpyAsync(static_cast<char*>(I.buf[0]) + (size_t)f * I.p.fstride * c->elem,
                            static_cast<const char*>(src) + f * fb, fb, kind, c->stream),
            "state copy");
     int64_t t = 0;
@@ -578,7 +881,7 @@ tslb_status tslb_put_state(tslb_ctx* c, const void* src, int on_device) {
     CK(cudaMemcpyAsync(c->tdev, tt, sizeof(tt), cudaMemcpyHostToDevice, c->stream), "step counter");
     CK(cudaStreamSynchronize(c->stream), "put_state synchronise");
     c->t = t;
-    c->have_state = true;
+    I.set = true;
     c->parts_valid = false;
     c->since_check = 0;
     return TSLB_OK;
@@ -595,8 +898,7 @@ tslb_status tslb_destroy(tslb_ctx* c) {
     if (!c) return TSLB_OK;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (int k = 0; k < 2; ++k)
-        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    drop_graphs(c);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
@@ -623,5 +925,7 @@ const char* tslb_status_string(tslb_status s) {
 }
 
 int64_t tslb_kernel_launches(const tslb_ctx* c) { return c ? c->launches : 0; }
+
+int32_t tslb_batch_count(const tslb_ctx* c) { return c ? (int32_t)c->inst.size() : 0; }
 
 }  // extern "C"

@@ -21,12 +21,19 @@ struct StepParams {
     int nx, ny, nz;
     int face[6];
     int tile_z;
+    int block_warps;         // warps per block of the step kernel (8, 12 or 16)
     long long fstride;       // elements between consecutive fields of a buffer
     float omega, sigma, gamma, normal_eps2;
     float inlet_u[3], inlet_umag, inlet_half_d, inlet_cx, inlet_cy, inlet_two_over_w, noise_amp;
     unsigned seed_lo, seed_hi;
     float scale[NFIELDS];    // 16-bit storage: stored = scale * value
     float inv_scale[NFIELDS];
+};
+
+// One grid of a batch: its parameters and its two state buffers.
+struct BatchInstance {
+    StepParams p;
+    const void* buf[2];
 };
 
 struct LaunchShape {
@@ -64,6 +71,14 @@ cudaError_t launch_finish_sums(const double* partials, int n, double* result, cu
 
 // Largest number of partial pairs any launch above writes for this grid.
 int max_partials(const StepParams& p, int storage);
+
+// Batched FP32 step: tiles[k] = (instance, bx, by, bz) over all instances,
+// taken from counters[parity] by `nblocks` persistent blocks of `nw` warps
+// (8 or 12); tile k writes partials[2k..2k+1].
+cudaError_t prepare_batch_kernels();
+cudaError_t launch_batch_step(int nw, const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
+                              const long long* t_in, long long* t_out, int* counters, double* partials,
+                              int nblocks, cudaStream_t s);
 
 // Message returned by tslb_last_error(NULL) (calls that have no context).
 void set_global_error(const char* msg);

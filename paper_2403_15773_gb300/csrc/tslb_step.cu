@@ -47,7 +47,6 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TX = 30;        // interior columns of a tile; a warp stages TX + 2
 constexpr int PHX = TX + 4;   // phase-field columns of a tile (halo 2)
-constexpr int NW_STEP = 16;   // warps (staged rows) per block of the step kernel
 
 // ------------------------------------------------------------------ helpers
 
@@ -129,6 +128,7 @@ struct Io;
 template <>
 struct Io<float> {
     static constexpr bool kAsync = true;
+    static __device__ __forceinline__ float from_raw(unsigned short, float) { return 0.f; }
     static __device__ __forceinline__ float ld(const float* p, float) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
     static __device__ __forceinline__ float round_trip(float v, float, float) { return v; }
@@ -136,6 +136,9 @@ struct Io<float> {
 template <>
 struct Io<__half> {
     static constexpr bool kAsync = false;
+    static __device__ __forceinline__ float from_raw(unsigned short r, float inv) {
+        return __half2float(__ushort_as_half(r)) * inv;
+    }
     static __device__ __forceinline__ float ld(const __half* p, float inv) { return __half2float(__ldg(p)) * inv; }
     static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
     static __device__ __forceinline__ float round_trip(float v, float s, float inv) {
@@ -145,6 +148,9 @@ struct Io<__half> {
 template <>
 struct Io<__nv_bfloat16> {
     static constexpr bool kAsync = false;
+    static __device__ __forceinline__ float from_raw(unsigned short r, float inv) {
+        return __bfloat162float(__ushort_as_bfloat16(r)) * inv;
+    }
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p, float inv) {
         return __bfloat162float(__ldg(p)) * inv;
     }
@@ -154,55 +160,79 @@ struct Io<__nv_bfloat16> {
     }
 };
 
+// ------------------------------------------------------- packed FP32 helpers
+
+// Two lattice nodes per thread (rows 2w and 2w+1 of the tile) are processed
+// together with the packed FP32 instructions of sm_100+ (one instruction, two
+// lanes of arithmetic): .x is the node of row 2w, .y the node of row 2w+1.
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 operator*(float s, float2 b) { return __fmul2_rn(make_float2(s, s), b); }
+__device__ __forceinline__ float2 mad(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mad(float s, float2 b, float2 c) { return __ffma2_rn(make_float2(s, s), b, c); }
+__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+__device__ __forceinline__ float2 shfl_up2(float2 v) {
+    return make_float2(__shfl_up_sync(FULL, v.x, 1), __shfl_up_sync(FULL, v.y, 1));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v) {
+    return make_float2(__shfl_down_sync(FULL, v.x, 1), __shfl_down_sync(FULL, v.y, 1));
+}
+
 // One axis of the streaming sweep.  (k0, k1, k2) are the Hermite coefficients
 // of the axis (k2 pre-multiplied by h2(+-1) = 2/3); the unnormalised 1D
 // populations (x 6) are
-//   p(-1) = k0 - k1 + k2,   p(0) = 4 k0 - 2 k2,   p(+1) = k0 + k1 + k2.
-struct Tri {
-    float m, z, p;
+//   p(-1) = k0 - k1 + k2,   p(0) = 4 k0 - 2 k2,   p(+1) = k0 + k1 + k2,
+// and after the shift the raw moments of the axis are
+//   M0 = q- + q0 + q+,   M1 = q+ - q-,   M2 = q+ + q-.
+struct Tri2 {
+    float2 m, z, p;
 };
-__device__ __forceinline__ Tri pops3(float k0, float k1, float k2) {
-    return {k0 - k1 + k2, 4.f * k0 - 2.f * k2, k0 + k1 + k2};
+__device__ __forceinline__ Tri2 pops2(float2 k0, float2 k1, float2 k2) {
+    const float2 s = k0 + k2;
+    return {s - k1, mad(4.f, k0, -2.f * k2), s + k1};
 }
-
-// x sweep: shift p(+1) one lane up and p(-1) one lane down, then the x raw
-// moments (x 6) M0 = q- + q0 + q+, M1 = q+ - q-, M2 = q+ + q-.
-__device__ __forceinline__ void xsweep(float k0, float k1, float k2, float& m0, float& m1, float& m2) {
-    const Tri t = pops3(k0, k1, k2);
-    const float qp = __shfl_up_sync(FULL, t.p, 1);
-    const float qm = __shfl_down_sync(FULL, t.m, 1);
-    m0 = qm + t.z + qp;
+// x sweep of two nodes: shifts along the warp (lanes = x), then x moments.
+__device__ __forceinline__ void xsweep2(float2 k0, float2 k1, float2 k2, float2& m0, float2& m1, float2& m2) {
+    const Tri2 t = pops2(k0, k1, k2);
+    const float2 qp = shfl_up2(t.p), qm = shfl_down2(t.m);
+    const float2 s = qp + qm;
+    m0 = s + t.z;
     m1 = qp - qm;
-    m2 = qp + qm;
+    m2 = s;
 }
+__device__ __forceinline__ float2 s0v(float2 a, float2 b, float2 c) { return mad(4.f, b, a + c); }
+__device__ __forceinline__ float2 l2v(float2 a, float2 b, float2 c) { return mad(-2.f, b, a + c); }
 
-__device__ __forceinline__ float s0(const float* v) { return v[0] + 4.f * v[1] + v[2]; }
-__device__ __forceinline__ float d1(const float* v) { return v[2] - v[0]; }
-__device__ __forceinline__ float l2(const float* v) { return v[0] + v[2] - 2.f * v[1]; }
-
-// ---------------------------------------------------------------- step kernel
+// ----------------------------------------------------- step kernel (pairs)
 
 template <int NW>
-struct StepSmem {
-    static constexpr int NT = 32 * NW;
-    static constexpr int NPH = PHX * (NW + 2);
-    static constexpr int RING = 0;                 // [4][NPH] phase-field planes
-    static constexpr int ZC = RING + 4 * NPH;      // [2][3][NPH] z combinations of phi
-    static constexpr int MOM = ZC + 6 * NPH;       // [2][10][NT] staged moments
-    static constexpr int YX = MOM + 20 * NT;       // [2][20][NT] y exchange
+struct Step2Smem {
+    static constexpr int NT = 32 * NW;              // threads
+    static constexpr int NR = 2 * NW;               // staged rows (two per warp)
+    static constexpr int NS = 32 * NR;              // staged nodes
+    static constexpr int NPH = PHX * (NR + 2);      // phase-field elements (halo 2)
+    static constexpr int RING = 0;                  // [4][NPH] phase-field planes
+    static constexpr int ZC = RING + 4 * NPH;       // [2][3][NPH] z combinations of phi
+    static constexpr int MOM = ZC + 6 * NPH;        // [2][10][NS] staged moments
+    static constexpr int YX = MOM + 20 * NS;        // [2][20][NT] y exchange
     static constexpr int FLOATS = YX + 40 * NT;
     static constexpr size_t BYTES = sizeof(float) * FLOATS;
 };
 
+// One tile of one time step: the 30 x (2 NW - 2) interior columns at tile
+// (bx, by), planes [bz * tile_z, (bz + 1) * tile_z), from state `in` (step t)
+// to state `out`; writes the tile's FP64 partial sums to part[0..1].
 template <int NW, typename S>
-__global__ void __launch_bounds__(32 * NW, 1)
-    step_kernel(const __grid_constant__ StepParams P, const S* __restrict__ in, S* __restrict__ out,
-                const long long* __restrict__ t_in, long long* __restrict__ t_out,
-                double* __restrict__ partials) {
-    using L = StepSmem<NW>;
-    constexpr int NT = L::NT;
-    constexpr int NPH = L::NPH;
-    constexpr int TY = NW - 2;
+__device__ __forceinline__ void step_tile(const StepParams& P, const S* __restrict__ in, S* __restrict__ out,
+                                          const long long t, const int bx, const int by, const int bz,
+                                          double* __restrict__ part) {
+    using L = Step2Smem<NW>;
+    constexpr int NT = L::NT, NR = L::NR, NS = L::NS, NPH = L::NPH;
+    constexpr int TY = NR - 2;
     constexpr int EPT = (NPH + NT - 1) / NT;
     extern __shared__ __align__(16) float smem[];
     float* const ring = smem + L::RING;
@@ -210,26 +240,27 @@ __global__ void __launch_bounds__(32 * NW, 1)
     float* const mom = smem + L::MOM;
     float* const yx = smem + L::YX;
 
-    const int lane = threadIdx.x, warp = threadIdx.y, tid = lane + 32 * warp;
+    const int lane = threadIdx.x, w = threadIdx.y, tid = lane + 32 * w;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
     const long long nxy = (long long)nx * ny;
     const long long fs = P.fstride;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * P.tile_z;
+    const int x0 = bx * TX, y0 = by * TY, z0 = bz * P.tile_z;
     const int z1 = min(z0 + P.tile_z, nz);
-    const long long t = *t_in;
 
-    // staged node of this thread (constant along the march)
+    // the two staged nodes of this thread (constant along the march)
     int unused = 0;
-    float sgx, sgy;
-    const int gx = x0 - 1 + lane, gy = y0 - 1 + warp;
+    float sgx, sgyA, sgyB;
+    const int gx = x0 - 1 + lane, gyA = y0 - 1 + 2 * w, gyB = gyA + 1;
     const int sx = resolve_axis(gx, nx, P.face[0], P.face[1], sgx, unused);
-    const int sy = resolve_axis(gy, ny, P.face[2], P.face[3], sgy, unused);
-    const long long sxy = sx + (long long)nx * sy;
-    const bool row_interior = warp >= 1 && warp <= NW - 2;
-    const bool store_ok = row_interior && lane >= 1 && lane <= TX && gx < nx && gy < ny;
+    const int syA = resolve_axis(gyA, ny, P.face[2], P.face[3], sgyA, unused);
+    const int syB = resolve_axis(gyB, ny, P.face[2], P.face[3], sgyB, unused);
+    const int sxyA = sx + nx * syA, sxyB = sx + nx * syB;  // < 2^31: the plane size is checked on the host
+    const bool col_ok = lane >= 1 && lane <= TX && gx < nx;
+    const bool storeA = col_ok && w >= 1 && gyA < ny;       // staged row 2w is interior for w >= 1
+    const bool storeB = col_ok && w <= NW - 2 && gyB < ny;  // staged row 2w+1 for w <= NW-2
+    const int sA = lane + 64 * w;                           // staged-node slot of row 2w (row 2w+1: +32)
 
-    // phase-field elements loaded by this thread (columns x0-2.., rows y0-2..)
-    long long pxy[EPT];
+    int pxy[EPT];
     float phib[EPT];
     const bool inlet_planes = P.face[4] == BC_INLET && z0 < 2;
 #pragma unroll
@@ -241,17 +272,24 @@ __global__ void __launch_bounds__(32 * NW, 1)
             float sg;
             const int psx = resolve_axis(x0 - 2 + idx % PHX, nx, P.face[0], P.face[1], sg, unused);
             const int psy = resolve_axis(y0 - 2 + idx / PHX, ny, P.face[2], P.face[3], sg, unused);
-            pxy[e] = psx + (long long)nx * psy;
+            pxy[e] = psx + nx * psy;
             if (inlet_planes) phib[e] = inlet_phi(P, psx, psy);
         }
     }
 
-    auto load_phi_plane = [&](int q) {
+    // FP32: cp.async straight into shared memory, one plane ahead.  16-bit
+    // storage: the next plane's raw values wait in registers while the
+    // current plane is computed and are widened into the same shared-memory
+    // slots afterwards (each slot is read only by the thread that fills it).
+    unsigned short rphi[EPT], rmom[2][10];
+    int rphi_inl = 0;
+    auto issue_phi = [&](int q) {
         float sg;
         int inl = 0;
         const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);
         float* dst = ring + ((q + 8) & 3) * NPH;
         const S* src = in + F_PHI * fs + nxy * sz;
+        rphi_inl = inl;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const int idx = tid + e * NT;
@@ -261,52 +299,77 @@ __global__ void __launch_bounds__(32 * NW, 1)
                 } else if constexpr (Io<S>::kAsync) {
                     cp_async4(dst + idx, reinterpret_cast<const float*>(src + pxy[e]));
                 } else {
-                    dst[idx] = Io<S>::ld(src + pxy[e], P.inv_scale[F_PHI]);
+                    rphi[e] = __ldg(reinterpret_cast<const unsigned short*>(src + pxy[e]));
                 }
             }
         }
     };
-    auto load_mom_plane = [&](int q, float& sgz, int& inl) {
+    auto commit_phi = [&](int q) {
+        if constexpr (!Io<S>::kAsync) {
+            if (!rphi_inl) {
+                float* dst = ring + ((q + 8) & 3) * NPH;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) {
+                    const int idx = tid + e * NT;
+                    if (idx < NPH) dst[idx] = Io<S>::from_raw(rphi[e], P.inv_scale[F_PHI]);
+                }
+            }
+        }
+    };
+    auto issue_mom = [&](int q, float& sgz, int& inl) {
         inl = 0;
         const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sgz, inl);
-        float* dst = mom + ((q + 8) & 1) * 10 * NT + tid;
-        const S* src = in + sxy + nxy * sz;
+        float* dst = mom + ((q + 8) & 1) * 10 * NS + sA;
+        const S* srcA = in + nxy * sz + sxyA;
+        const S* srcB = in + nxy * sz + sxyB;
 #pragma unroll
         for (int f = 0; f < 10; ++f) {
-            if constexpr (Io<S>::kAsync)
-                cp_async4(dst + f * NT, reinterpret_cast<const float*>(src + f * fs));
-            else
-                dst[f * NT] = Io<S>::ld(src + f * fs, P.inv_scale[f]);
+            if constexpr (Io<S>::kAsync) {
+                cp_async4(dst + f * NS, reinterpret_cast<const float*>(srcA + f * fs));
+                cp_async4(dst + f * NS + 32, reinterpret_cast<const float*>(srcB + f * fs));
+            } else {
+                rmom[0][f] = __ldg(reinterpret_cast<const unsigned short*>(srcA + f * fs));
+                rmom[1][f] = __ldg(reinterpret_cast<const unsigned short*>(srcB + f * fs));
+            }
+        }
+    };
+    auto commit_mom = [&](int q) {
+        if constexpr (!Io<S>::kAsync) {
+            float* dst = mom + ((q + 8) & 1) * 10 * NS + sA;
+#pragma unroll
+            for (int f = 0; f < 10; ++f) {
+                dst[f * NS] = Io<S>::from_raw(rmom[0][f], P.inv_scale[f]);
+                dst[f * NS + 32] = Io<S>::from_raw(rmom[1][f], P.inv_scale[f]);
+            }
         }
     };
 
     float sgz_cur, sgz_nxt;
     int inl_cur, inl_nxt;
-    load_phi_plane(z0 - 2);
-    load_phi_plane(z0 - 1);
-    load_phi_plane(z0);
-    load_mom_plane(z0 - 1, sgz_cur, inl_cur);
+    for (int q = z0 - 2; q <= z0; ++q) {
+        issue_phi(q);
+        commit_phi(q);
+    }
+    issue_mom(z0 - 1, sgz_cur, inl_cur);
+    commit_mom(z0 - 1);
     cp_async_commit();
 
-    // z-march carries: for each (qx, qy) group the z populations p(+1) of the
-    // two previous planes and p(0) of the previous plane; same for D3Q7.
-    float cPP[6], cP[6], cZ[6];
+    float2 cPP[6], cP[6], cZ[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) cPP[k] = cP[k] = cZ[k] = 0.f;
-    float cH = 0.f, cVPP = 0.f, cVP = 0.f;
+    for (int k = 0; k < 6; ++k) cPP[k] = cP[k] = cZ[k] = bc(0.f);
+    float2 cH = bc(0.f), cVPP = bc(0.f), cVP = bc(0.f);
     float sum_rho = 0.f, sum_phi = 0.f;
 
     const float om1 = 1.f - P.omega, fo = 1.f - 0.5f * P.omega;
+    const float sig_half = -0.5f * P.sigma;
     int buf = 0;
     for (int p = z0 - 1; p <= z1; ++p) {
-        load_phi_plane(p + 2);
-        load_mom_plane(p + 1, sgz_nxt, inl_nxt);
+        issue_phi(p + 2);
+        issue_mom(p + 1, sgz_nxt, inl_nxt);
         cp_async_commit();
         cp_async_wait<1>();
 
-        // (1) z combinations of phi at plane p for the elements of this thread:
-        //     phi, phi(z+1) + phi(z-1), phi(z+1) - phi(z-1)
-        {
+        {  // z combinations of phi at plane p
             const float* pm = ring + ((p - 1 + 8) & 3) * NPH;
             const float* pc = ring + ((p + 8) & 3) * NPH;
             const float* pp = ring + ((p + 1 + 8) & 3) * NPH;
@@ -324,177 +387,196 @@ __global__ void __launch_bounds__(32 * NW, 1)
         }
         __syncthreads();
 
-        // (2)-(4a) staged node: interface geometry, post-collision Hermite
-        //          coefficients, x sweep, y populations.
-        float YZ[9];
-        float hx, vzp, vzm;
+        float2 YZ[9];      // y populations p(0) of the (qx, c) groups
+        float PA[9], MB[9];  // p(+1) of row 2w (-> row 2w+1), p(-1) of row 2w+1 (-> row 2w)
+        float2 hx, vzp, vzm;
+        float dyA, dyB;    // D3Q7 y terms kept in the thread
         {
-            const float* m = mom + ((p + 8) & 1) * 10 * NT + tid;
-            const float drho = m[0];
-            float ux = m[NT] * sgx, uy = m[2 * NT] * sgy, uz = m[3 * NT] * sgz_cur;
-            const float pxx = m[4 * NT], pyy = m[5 * NT], pzz = m[6 * NT];
-            const float pxy = m[7 * NT] * (sgx * sgy), pxz = m[8 * NT] * (sgx * sgz_cur),
-                        pyz = m[9 * NT] * (sgy * sgz_cur);
+            const float* m = mom + ((p + 8) & 1) * 10 * NS + sA;
+            auto ld2 = [&](int f) { return make_float2(m[f * NS], m[f * NS + 32]); };
+            const float2 sgy = make_float2(sgyA, sgyB);
+            const float2 drho = ld2(0);
+            float2 ux = sgx * ld2(1), uy = sgy * ld2(2), uz = sgz_cur * ld2(3);
+            const float2 pxx = ld2(4), pyy = ld2(5), pzz = ld2(6);
+            const float2 pxy = (sgx * sgy) * ld2(7), pxz = (sgx * sgz_cur) * ld2(8), pyz = (sgz_cur * sgy) * ld2(9);
             if (inl_cur) {
-                float ub[3];
-                inlet_velocity(P, sx, sy, t, ub);
-                ux = ub[0] * sgx;
-                uy = ub[1] * sgy;
-                uz = ub[2];
+                float ua[3], ub[3];
+                inlet_velocity(P, sx, syA, t, ua);
+                inlet_velocity(P, sx, syB, t, ub);
+                ux = make_float2(ua[0] * sgx, ub[0] * sgx);
+                uy = make_float2(ua[1] * sgyA, ub[1] * sgyB);
+                uz = make_float2(ua[2], ub[2]);
             }
 
-            // isotropic stencils of grad phi and its Hessian, separably:
-            // z combos from shared memory, then y, then x (all x 216 / weights)
+            // grad phi and Hessian: z combos from shared memory (rows 2w-1 .. 2w+2
+            // of the tile), then y combos for the row pair, then x combos
             const float* zb = zc + buf * 3 * NPH;
-            const int e0 = (lane + 1) + PHX * (warp + 1);
-            float yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
+            float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
-                float zS[3], zD[3], zL[3];
+                float zS[4], zD[4], zL[4];
 #pragma unroll
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int e = e0 + dx + PHX * dy;
+                for (int r = 0; r < 4; ++r) {
+                    const int e = (lane + 1 + dx) + PHX * (2 * w + r);
                     const float c0 = zb[e], c1 = zb[NPH + e], c2 = zb[2 * NPH + e];
-                    zS[dy + 1] = c1 + 4.f * c0;
-                    zD[dy + 1] = c2;
-                    zL[dy + 1] = c1 - 2.f * c0;
+                    zS[r] = fmaf(4.f, c0, c1);
+                    zD[r] = c2;
+                    zL[r] = fmaf(-2.f, c0, c1);
                 }
-                yS[dx + 1] = s0(zS);
-                yDS[dx + 1] = d1(zS);
-                yLS[dx + 1] = l2(zS);
-                ySD[dx + 1] = s0(zD);
-                yDD[dx + 1] = d1(zD);
-                ySL[dx + 1] = s0(zL);
+                const float2 sm = make_float2(zS[0], zS[1]), s0 = make_float2(zS[1], zS[2]),
+                             sp = make_float2(zS[2], zS[3]);
+                const float2 dm = make_float2(zD[0], zD[1]), d0 = make_float2(zD[1], zD[2]),
+                             dp = make_float2(zD[2], zD[3]);
+                const float2 lm = make_float2(zL[0], zL[1]), l0 = make_float2(zL[1], zL[2]),
+                             lp = make_float2(zL[2], zL[3]);
+                yS[dx + 1] = s0v(sm, s0, sp);
+                yDS[dx + 1] = sp - sm;
+                yLS[dx + 1] = l2v(sm, s0, sp);
+                ySD[dx + 1] = s0v(dm, d0, dp);
+                yDD[dx + 1] = dp - dm;
+                ySL[dx + 1] = s0v(lm, l0, lp);
             }
-            const float phi = zb[e0];
-            const float gxp = d1(yS) * (1.f / 72.f), gyp = s0(yDS) * (1.f / 72.f),
-                        gzp = s0(ySD) * (1.f / 72.f);
-            const float hxx = l2(yS) * (1.f / 36.f), hyy = s0(yLS) * (1.f / 36.f),
-                        hzz = s0(ySL) * (1.f / 36.f);
-            const float hxy = d1(yDS) * (1.f / 24.f), hxz = d1(ySD) * (1.f / 24.f),
-                        hyz = s0(yDD) * (1.f / 24.f);
+            const int ec = (lane + 1) + PHX * (2 * w + 1);
+            const float2 phi = make_float2(zb[ec], zb[ec + PHX]);
+            const float2 gxp = (1.f / 72.f) * (yS[2] - yS[0]);
+            const float2 gyp = (1.f / 72.f) * s0v(yDS[0], yDS[1], yDS[2]);
+            const float2 gzp = (1.f / 72.f) * s0v(ySD[0], ySD[1], ySD[2]);
+            const float2 hxx = (1.f / 36.f) * l2v(yS[0], yS[1], yS[2]);
+            const float2 hyy = (1.f / 36.f) * s0v(yLS[0], yLS[1], yLS[2]);
+            const float2 hzz = (1.f / 36.f) * s0v(ySL[0], ySL[1], ySL[2]);
+            const float2 hxy = (1.f / 24.f) * (yDS[2] - yDS[0]);
+            const float2 hxz = (1.f / 24.f) * (ySD[2] - ySD[0]);
+            const float2 hyz = (1.f / 24.f) * s0v(yDD[0], yDD[1], yDD[2]);
 
-            // regularised normal, its divergence and the CSF force
-            const float m2 = gxp * gxp + gyp * gyp + gzp * gzp + P.normal_eps2;
-            const float im = m2 > 0.f ? rsqrtf(m2) : 0.f;
-            float nxv = gxp * im, nyv = gyp * im, nzv = gzp * im;
-            const float ghg = gxp * (gxp * hxx + 2.f * (gyp * hxy + gzp * hxz)) +
-                              gyp * (gyp * hyy + 2.f * gzp * hyz) + gzp * gzp * hzz;
-            const float kappa = (hxx + hyy + hzz) * im - ghg * (im * im * im);
-            const float fk = -0.5f * P.sigma * kappa;
-            float Fx = fk * gxp, Fy = fk * gyp, Fz = fk * gzp;
+            // regularised normal, curvature, CSF force
+            const float2 m2 = mad(gxp, gxp, mad(gyp, gyp, mad(gzp, gzp, bc(P.normal_eps2))));
+            const float2 im = make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
+            float2 nxv = gxp * im, nyv = gyp * im, nzv = gzp * im;
+            const float2 ghg = mad(gxp, mad(gxp, hxx, 2.f * mad(gyp, hxy, gzp * hxz)),
+                                   mad(gyp, mad(gyp, hyy, 2.f * (gzp * hyz)), gzp * gzp * hzz));
+            const float2 kappa = (hxx + hyy + hzz) * im - ghg * (im * im * im);
+            const float2 fk = sig_half * kappa;
+            float2 Fx = fk * gxp, Fy = fk * gyp, Fz = fk * gzp;
             if (inl_cur) {
-                Fx = Fy = Fz = 0.f;
-                nxv = nyv = nzv = 0.f;
+                Fx = Fy = Fz = bc(0.f);
+                nxv = nyv = nzv = bc(0.f);
             }
 
             // collision in Hermite form (Guo forcing: v = u + F / (2 rho))
-            const float rho = 1.f + drho, irho = 1.f / rho;
-            const float hfx = 0.5f * Fx * irho, hfy = 0.5f * Fy * irho, hfz = 0.5f * Fz * irho;
-            const float vx = ux + hfx, vy = uy + hfy, vz = uz + hfz;
-            // Pi^neq relative to v: P + rho (u u - v v) = P - rho (u h + h v)
-            const float nxx = pxx - rho * (ux * hfx + hfx * vx);
-            const float nyy = pyy - rho * (uy * hfy + hfy * vy);
-            const float nzz = pzz - rho * (uz * hfz + hfz * vz);
-            const float nxy = pxy - rho * (ux * hfy + hfx * vy);
-            const float nxz = pxz - rho * (ux * hfz + hfx * vz);
-            const float nyz = pyz - rho * (uy * hfz + hfy * vz);
-            const float rvx = rho * vx, rvy = rho * vy, rvz = rho * vz;
-            // A2 = rho v v + (1-omega) Pi^neq + (1-omega/2)(v F + F v)
-            // M  = rho v v / 3 + (1-omega) Pi^neq  (A3 = v M + M v + ... )
-            const float exx = rvx * vx, eyy = rvy * vy, ezz = rvz * vz;
-            const float exy = rvx * vy, exz = rvx * vz, eyz = rvy * vz;
-            const float Mxx = exx * (1.f / 3.f) + om1 * nxx, Myy = eyy * (1.f / 3.f) + om1 * nyy,
-                        Mzz = ezz * (1.f / 3.f) + om1 * nzz, Mxy = exy * (1.f / 3.f) + om1 * nxy,
-                        Mxz = exz * (1.f / 3.f) + om1 * nxz, Myz = eyz * (1.f / 3.f) + om1 * nyz;
-            const float A2xx = exx + om1 * nxx + fo * (2.f * vx * Fx);
-            const float A2yy = eyy + om1 * nyy + fo * (2.f * vy * Fy);
-            const float A2zz = ezz + om1 * nzz + fo * (2.f * vz * Fz);
-            const float A2xy = exy + om1 * nxy + fo * (vx * Fy + Fx * vy);
-            const float A2xz = exz + om1 * nxz + fo * (vx * Fz + Fx * vz);
-            const float A2yz = eyz + om1 * nyz + fo * (vy * Fz + Fy * vz);
+            const float2 rho = bc(1.f) + drho;
+            const float2 irho = rcp2(rho);
+            const float2 hf = 0.5f * irho;
+            const float2 hfx = hf * Fx, hfy = hf * Fy, hfz = hf * Fz;
+            const float2 vx = ux + hfx, vy = uy + hfy, vz = uz + hfz;
+            const float2 nxx = pxx - rho * mad(ux, hfx, hfx * vx);
+            const float2 nyy = pyy - rho * mad(uy, hfy, hfy * vy);
+            const float2 nzz = pzz - rho * mad(uz, hfz, hfz * vz);
+            const float2 nxy = pxy - rho * mad(ux, hfy, hfx * vy);
+            const float2 nxz = pxz - rho * mad(ux, hfz, hfx * vz);
+            const float2 nyz = pyz - rho * mad(uy, hfz, hfy * vz);
+            const float2 rvx = rho * vx, rvy = rho * vy, rvz = rho * vz;
+            const float2 exx = rvx * vx, eyy = rvy * vy, ezz = rvz * vz;
+            const float2 exy = rvx * vy, exz = rvx * vz, eyz = rvy * vz;
+            const float2 o1 = bc(om1), third = bc(1.f / 3.f);
+            const float2 qxx = o1 * nxx, qyy = o1 * nyy, qzz = o1 * nzz;
+            const float2 qxy = o1 * nxy, qxz = o1 * nxz, qyz = o1 * nyz;
+            const float2 Mxx = mad(third, exx, qxx), Myy = mad(third, eyy, qyy), Mzz = mad(third, ezz, qzz);
+            const float2 Mxy = mad(third, exy, qxy), Mxz = mad(third, exz, qxz), Myz = mad(third, eyz, qyz);
+            const float2 f2o = bc(2.f * fo), f1o = bc(fo);
+            const float2 A2xx = mad(f2o, vx * Fx, exx + qxx);
+            const float2 A2yy = mad(f2o, vy * Fy, eyy + qyy);
+            const float2 A2zz = mad(f2o, vz * Fz, ezz + qzz);
+            const float2 A2xy = mad(f1o, mad(vx, Fy, Fx * vy), exy + qxy);
+            const float2 A2xz = mad(f1o, mad(vx, Fz, Fx * vz), exz + qxz);
+            const float2 A2yz = mad(f1o, mad(vy, Fz, Fy * vz), eyz + qyz);
 
-            // Hermite coefficients of the tensor-product basis h_a(cx) h_b(cy) h_c(cz),
-            // index 2 pre-multiplied by 2/3:  k_abc
-            const float k000 = drho;
-            const float k100 = 3.f * (rho * ux + Fx), k010 = 3.f * (rho * uy + Fy),
-                        k001 = 3.f * (rho * uz + Fz);
-            const float k200 = 3.f * A2xx, k020 = 3.f * A2yy, k002 = 3.f * A2zz;
-            const float k110 = 9.f * A2xy, k101 = 9.f * A2xz, k011 = 9.f * A2yz;
-            const float k210 = 9.f * (2.f * vx * Mxy + vy * Mxx);
-            const float k201 = 9.f * (2.f * vx * Mxz + vz * Mxx);
-            const float k120 = 9.f * (2.f * vy * Mxy + vx * Myy);
-            const float k021 = 9.f * (2.f * vy * Myz + vz * Myy);
-            const float k102 = 9.f * (2.f * vz * Mxz + vx * Mzz);
-            const float k012 = 9.f * (2.f * vz * Myz + vy * Mzz);
-            const float k111 = 27.f * (vx * Myz + vy * Mxz + vz * Mxy);
+            // tensor-product Hermite coefficients k_abc, index 2 pre-multiplied by
+            // 2/3, everything pre-divided by 216 (the 6^3 of the unnormalised sweeps)
+            const float2 c72 = bc(1.f / 72.f), c24 = bc(1.f / 24.f);
+            const float2 k000 = (1.f / 216.f) * drho;
+            const float2 k100 = c72 * mad(rho, ux, Fx), k010 = c72 * mad(rho, uy, Fy), k001 = c72 * mad(rho, uz, Fz);
+            const float2 k200 = c72 * A2xx, k020 = c72 * A2yy, k002 = c72 * A2zz;
+            const float2 k110 = c24 * A2xy, k101 = c24 * A2xz, k011 = c24 * A2yz;
+            const float2 tx = 2.f * vx, ty = 2.f * vy, tz = 2.f * vz;
+            const float2 k210 = c24 * mad(tx, Mxy, vy * Mxx);
+            const float2 k201 = c24 * mad(tx, Mxz, vz * Mxx);
+            const float2 k120 = c24 * mad(ty, Mxy, vx * Myy);
+            const float2 k021 = c24 * mad(ty, Myz, vz * Myy);
+            const float2 k102 = c24 * mad(tz, Mxz, vx * Mzz);
+            const float2 k012 = c24 * mad(tz, Myz, vy * Mzz);
+            const float2 k111 = (1.f / 8.f) * mad(vx, Myz, mad(vy, Mxz, vz * Mxy));
 
-            // x sweep: X[qx][g], g = b + 3 c over the (b, c) pairs present
-            float X[3][8];
-            xsweep(k000, k100, k200, X[0][0], X[1][0], X[2][0]);
-            xsweep(k010, k110, k210, X[0][1], X[1][1], X[2][1]);
-            xsweep(k020, k120, 0.f, X[0][2], X[1][2], X[2][2]);
-            xsweep(k001, k101, k201, X[0][3], X[1][3], X[2][3]);
-            xsweep(k011, k111, 0.f, X[0][4], X[1][4], X[2][4]);
-            xsweep(k021, 0.f, 0.f, X[0][5], X[1][5], X[2][5]);
-            xsweep(k002, k102, 0.f, X[0][6], X[1][6], X[2][6]);
-            xsweep(k012, 0.f, 0.f, X[0][7], X[1][7], X[2][7]);
+            float2 X[3][8];
+            const float2 zero = bc(0.f);
+            xsweep2(k000, k100, k200, X[0][0], X[1][0], X[2][0]);
+            xsweep2(k010, k110, k210, X[0][1], X[1][1], X[2][1]);
+            xsweep2(k020, k120, zero, X[0][2], X[1][2], X[2][2]);
+            xsweep2(k001, k101, k201, X[0][3], X[1][3], X[2][3]);
+            xsweep2(k011, k111, zero, X[0][4], X[1][4], X[2][4]);
+            xsweep2(k021, zero, zero, X[0][5], X[1][5], X[2][5]);
+            xsweep2(k002, k102, zero, X[0][6], X[1][6], X[2][6]);
+            xsweep2(k012, zero, zero, X[0][7], X[1][7], X[2][7]);
 
-            // y populations of each (qx, c) group; p(+1) and p(-1) go to the
-            // rows below and above through shared memory
+            // y populations; the row pair exchanges inside the thread, the pair
+            // edges go through shared memory: p(+1) of row 2w+1 to the thread
+            // below, p(-1) of row 2w to the thread above
             float* yb = yx + buf * 20 * NT + tid;
 #pragma unroll
             for (int qx = 0; qx < 3; ++qx)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float b0 = X[qx][3 * c], b1 = X[qx][3 * c + 1];
-                    const float b2 = c < 2 ? X[qx][3 * c + 2] : 0.f;
-                    const Tri tr = pops3(b0, b1, b2);
+                    const float2 b0 = X[qx][3 * c], b1 = X[qx][3 * c + 1];
+                    const float2 b2 = c < 2 ? X[qx][3 * c + 2] : zero;
+                    const Tri2 tr = pops2(b0, b1, b2);
                     const int k = 3 * qx + c;
-                    yb[(2 * k) * NT] = tr.p;
-                    yb[(2 * k + 1) * NT] = tr.m;
+                    yb[(2 * k) * NT] = tr.p.y;
+                    yb[(2 * k + 1) * NT] = tr.m.x;
                     YZ[k] = tr.z;
+                    PA[k] = tr.p.x;
+                    MB[k] = tr.m.y;
                 }
 
             // D3Q7: g_i^post = w_i (B0 + c_i . B1)
-            const float ga = P.gamma * (1.f - phi * phi);
-            const float b1x = 4.f * phi * vx + ga * nxv;
-            const float b1y = 4.f * phi * vy + ga * nyv;
-            const float b1z = 4.f * phi * vz + ga * nzv;
-            const float fromL = __shfl_up_sync(FULL, phi + b1x, 1);
-            const float fromR = __shfl_down_sync(FULL, phi - b1x, 1);
-            hx = 0.25f * phi + 0.125f * (fromL + fromR);
-            yb[18 * NT] = phi + b1y;
-            yb[19 * NT] = phi - b1y;
+            const float2 ga = P.gamma * (bc(1.f) - phi * phi);
+            const float2 fphi = 4.f * phi;
+            const float2 b1x = mad(fphi, vx, ga * nxv);
+            const float2 b1y = mad(fphi, vy, ga * nyv);
+            const float2 b1z = mad(fphi, vz, ga * nzv);
+            const float2 fromL = shfl_up2(phi + b1x), fromR = shfl_down2(phi - b1x);
+            hx = mad(0.25f, phi, 0.125f * (fromL + fromR));
+            const float2 yp = phi + b1y, ym = phi - b1y;
+            yb[18 * NT] = yp.y;
+            yb[19 * NT] = ym.x;
+            dyA = ym.y;  // row 2w+1 -> row 2w
+            dyB = yp.x;  // row 2w -> row 2w+1
             vzp = phi + b1z;
             vzm = phi - b1z;
         }
         __syncthreads();
 
-        // (4b)-(5) interior rows: y shift and moments, z shift and moments,
-        //          output of plane p - 1.
-        if (row_interior) {
-            const float* ya = yx + buf * 20 * NT + tid - 32;  // row y - 1
-            const float* yc = yx + buf * 20 * NT + tid + 32;  // row y + 1
-            float Y[3][3][3];
+        {
+            const float* yprev = yx + buf * 20 * NT + (w > 0 ? tid - 32 : tid);       // row 2w-1
+            const float* ynext = yx + buf * 20 * NT + (w < NW - 1 ? tid + 32 : tid);  // row 2w+2
+            float2 Y[3][3][3];
 #pragma unroll
             for (int qx = 0; qx < 3; ++qx)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const int k = 3 * qx + c;
-                    const float qp = ya[(2 * k) * NT], qm = yc[(2 * k + 1) * NT];
-                    Y[qx][0][c] = qm + YZ[k] + qp;
+                    const float2 qp = make_float2(yprev[(2 * k) * NT], PA[k]);
+                    const float2 qm = make_float2(MB[k], ynext[(2 * k + 1) * NT]);
+                    const float2 s = qp + qm;
+                    Y[qx][0][c] = s + YZ[k];
                     Y[qx][1][c] = qp - qm;
-                    Y[qx][2][c] = qp + qm;
+                    Y[qx][2][c] = s;
                 }
-            const float hxy = hx + 0.125f * (ya[18 * NT] + yc[19 * NT]);
+            const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], dyB) + make_float2(dyA, ynext[19 * NT]), hx);
 
-            // z populations of the (qx, qy) groups 00, 10, 01, 20, 02, 11
             const int gqx[6] = {0, 1, 0, 2, 0, 1}, gqy[6] = {0, 0, 1, 0, 2, 1};
-            float O0[6], O1[6], O2[6];
+            float2 O0[6], O1[6], O2[6];
 #pragma unroll
             for (int g = 0; g < 6; ++g) {
-                const Tri tr = pops3(Y[gqx[g]][gqy[g]][0], Y[gqx[g]][gqy[g]][1], Y[gqx[g]][gqy[g]][2]);
+                const Tri2 tr = pops2(Y[gqx[g]][gqy[g]][0], Y[gqx[g]][gqy[g]][1], Y[gqx[g]][gqy[g]][2]);
                 O0[g] = cPP[g] + cZ[g] + tr.m;
                 O1[g] = cPP[g] - tr.m;
                 O2[g] = cPP[g] + tr.m;
@@ -502,38 +584,54 @@ __global__ void __launch_bounds__(32 * NW, 1)
                 cP[g] = tr.p;
                 cZ[g] = tr.z;
             }
-            const float phin = cH + 0.125f * (cVPP + vzm);
+            const float2 phin = mad(0.125f, cVPP + vzm, cH);
             cH = hxy;
             cVPP = cVP;
             cVP = vzp;
 
-            if (p >= z0 + 1 && store_ok) {
-                const float s = 1.f / 216.f;
-                const float dr = O0[0] * s, jx = O0[1] * s, jy = O0[2] * s, jz = O1[0] * s;
-                const float dxx = O0[3] * s, dyy = O0[4] * s, dzz = O2[0] * s;
-                const float cxy = O0[5] * s, cxz = O1[1] * s, cyz = O1[2] * s;
-                const float rn = 1.f + dr, irn = 1.f / rn;
-                const float ux = jx * irn, uy = jy * irn, uz = jz * irn;
-                const float val[NFIELDS] = {
-                    dr, ux, uy, uz,
-                    dxx - (1.f / 3.f) * dr - rn * ux * ux,
-                    dyy - (1.f / 3.f) * dr - rn * uy * uy,
-                    dzz - (1.f / 3.f) * dr - rn * uz * uz,
-                    cxy - rn * ux * uy, cxz - rn * ux * uz, cyz - rn * uy * uz, phin};
-                S* o = out + sxy + nxy * (p - 1);
+            if (p >= z0 + 1 && (storeA || storeB)) {
+                const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
+                const float2 rn = bc(1.f) + dr, irn = rcp2(rn);
+                const float2 ux = jx * irn, uy = jy * irn, uz = jz * irn;
+                const float2 rux = rn * ux, ruy = rn * uy, ruz = rn * uz;
+                const float2 mdr = (-1.f / 3.f) * dr;
+                float2 val[NFIELDS];
+                val[F_DRHO] = dr;
+                val[F_UX] = ux;
+                val[F_UY] = uy;
+                val[F_UZ] = uz;
+                val[F_PXX] = O0[3] + mdr - rux * ux;
+                val[F_PYY] = O0[4] + mdr - ruy * uy;
+                val[F_PZZ] = O2[0] + mdr - ruz * uz;
+                val[F_PXY] = O0[5] - rux * uy;
+                val[F_PXZ] = O1[1] - rux * uz;
+                val[F_PYZ] = O1[2] - ruy * uz;
+                val[F_PHI] = phin;
+                const long long zo = nxy * (p - 1);
+                if (storeA) {
+                    S* o = out + zo + sxyA;
 #pragma unroll
-                for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f], P.scale[f]);
-                sum_rho += Io<S>::round_trip(dr, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                sum_phi += Io<S>::round_trip(phin, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                    for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
+                    sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
+                    sum_phi += Io<S>::round_trip(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                }
+                if (storeB) {
+                    S* o = out + zo + sxyB;
+#pragma unroll
+                    for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
+                    sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
+                    sum_phi += Io<S>::round_trip(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                }
             }
         }
+        commit_phi(p + 2);
+        commit_mom(p + 1);
         sgz_cur = sgz_nxt;
         inl_cur = inl_nxt;
         buf ^= 1;
     }
     cp_async_wait<0>();
 
-    // block partials of sum(rho - 1) and sum(phi) in FP64
     double a = sum_rho, b = sum_phi;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -543,21 +641,69 @@ __global__ void __launch_bounds__(32 * NW, 1)
     __syncthreads();
     double* red = reinterpret_cast<double*>(yx);
     if (lane == 0) {
-        red[2 * warp] = a;
-        red[2 * warp + 1] = b;
+        red[2 * w] = a;
+        red[2 * w + 1] = b;
     }
     __syncthreads();
-    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (tid == 0) {
         double A = 0.0, B = 0.0;
-        for (int w = 0; w < NW; ++w) {
-            A += red[2 * w];
-            B += red[2 * w + 1];
+        for (int k = 0; k < NW; ++k) {
+            A += red[2 * k];
+            B += red[2 * k + 1];
         }
-        partials[2 * blk] = A;
-        partials[2 * blk + 1] = B;
-        if (blk == 0) *t_out = t + 1;
+        part[0] = A;
+        part[1] = B;
     }
+    __syncthreads();  // shared memory is reused by the block's next tile
+}
+
+// One time step of one grid: one block per tile.
+template <int NW, typename S>
+__global__ void __launch_bounds__(32 * NW, 1)
+    step2_kernel(const __grid_constant__ StepParams P, const S* __restrict__ in, S* __restrict__ out,
+                 const long long* __restrict__ t_in, long long* __restrict__ t_out,
+                 double* __restrict__ partials) {
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const long long t = *t_in;
+    step_tile<NW, S>(P, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+    if (blk == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_out = t + 1;
+}
+
+// One time step of a batch of independent grids in one persistent launch:
+// each block takes the next tile of the batch's tile list from a device
+// counter (tiles[k] = instance, bx, by, bz) until the list is exhausted.  The
+// instance's parameters are staged in shared memory for the tile.  counters[q]
+// serves the steps of parity q; each launch zeroes the other one for the next.
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 1)
+    step_batch_kernel(const BatchInstance* __restrict__ insts, const int4* __restrict__ tiles, int ntiles,
+                      int parity, const long long* __restrict__ t_in, long long* __restrict__ t_out,
+                      int* __restrict__ counters, double* __restrict__ partials) {
+    __shared__ StepParams sP;
+    __shared__ const float* s_io[2];
+    __shared__ int s_tile;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const long long t = *t_in;
+    if (blockIdx.x == 0 && tid == 0) counters[parity ^ 1] = 0;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&counters[parity], 1);
+        __syncthreads();
+        const int k = s_tile;
+        if (k >= ntiles) break;
+        const int4 tl = tiles[k];
+        {
+            const int* src = reinterpret_cast<const int*>(&insts[tl.x].p);
+            int* dst = reinterpret_cast<int*>(&sP);
+            for (int i = tid; i < (int)(sizeof(StepParams) / sizeof(int)); i += 32 * NW) dst[i] = src[i];
+            if (tid == 0) {
+                s_io[0] = static_cast<const float*>(insts[tl.x].buf[parity]);
+                s_io[1] = static_cast<const float*>(insts[tl.x].buf[parity ^ 1]);
+            }
+        }
+        __syncthreads();
+        step_tile<NW, float>(sP, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w, partials + 2 * k);
+    }
+    if (blockIdx.x == 0 && tid == 0) *t_out = t + 1;
 }
 
 // ------------------------------------------------------ state conversion
@@ -663,24 +809,71 @@ int conv_blocks(const StepParams& p) {
     return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
 }
 
+template <int NW, typename S>
+cudaError_t launch_nw(const StepParams& p, const void* in, void* out, const long long* t_in, long long* t_out,
+                      double* partials, cudaStream_t s) {
+    const LaunchShape sh = step_shape(p, ST_FP32);
+    step2_kernel<NW, S><<<sh.grid, sh.block, sh.smem, s>>>(p, static_cast<const S*>(in), static_cast<S*>(out),
+                                                           t_in, t_out, partials);
+    return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_step_t(const StepParams& p, const void* in, void* out, const long long* t_in,
                           long long* t_out, double* partials, cudaStream_t s) {
-    constexpr int NW = NW_STEP;
-    auto k = step_kernel<NW, S>;
-    const LaunchShape sh = step_shape(p, ST_FP32);
-    k<<<sh.grid, sh.block, sh.smem, s>>>(p, static_cast<const S*>(in), static_cast<S*>(out), t_in, t_out,
-                                         partials);
+    switch (p.block_warps) {
+        case 8: return launch_nw<8, S>(p, in, out, t_in, t_out, partials, s);
+        case 12: return launch_nw<12, S>(p, in, out, t_in, t_out, partials, s);
+        case 16: return launch_nw<16, S>(p, in, out, t_in, t_out, partials, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NW, typename S>
+cudaError_t prepare_nw() {
+    return cudaFuncSetAttribute(step2_kernel<NW, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Step2Smem<NW>::BYTES);
+}
+
+template <int NW>
+cudaError_t launch_batch_nw(const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
+                            const long long* t_in, long long* t_out, int* counters, double* partials, int nblocks,
+                            cudaStream_t s) {
+    step_batch_kernel<NW><<<nblocks, dim3(32, NW, 1), Step2Smem<NW>::BYTES, s>>>(insts, tiles, ntiles, parity, t_in,
+                                                                                  t_out, counters, partials);
     return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t prepare_t() {
-    return cudaFuncSetAttribute(step_kernel<NW_STEP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)StepSmem<NW_STEP>::BYTES);
+    cudaError_t e = prepare_nw<8, S>();
+    if (e == cudaSuccess) e = prepare_nw<12, S>();
+    if (e == cudaSuccess) e = prepare_nw<16, S>();
+    return e;
 }
 
 }  // namespace
+
+static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied as ints");
+
+cudaError_t prepare_batch_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(step_batch_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Step2Smem<8>::BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_batch_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Step2Smem<12>::BYTES);
+    return e;
+}
+
+cudaError_t launch_batch_step(int nw, const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
+                              const long long* t_in, long long* t_out, int* counters, double* partials,
+                              int nblocks, cudaStream_t s) {
+    switch (nw) {
+        case 8: return launch_batch_nw<8>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, nblocks, s);
+        case 12: return launch_batch_nw<12>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, nblocks, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t prepare_kernels(int storage) {
     switch (storage) {
@@ -691,18 +884,29 @@ cudaError_t prepare_kernels(int storage) {
     }
 }
 
+size_t step_smem_bytes(int nw) {
+    switch (nw) {
+        case 8: return Step2Smem<8>::BYTES;
+        case 12: return Step2Smem<12>::BYTES;
+        default: return Step2Smem<16>::BYTES;
+    }
+}
+
 LaunchShape step_shape(const StepParams& p, int /*storage*/) {
     LaunchShape sh;
-    sh.nw = NW_STEP;
-    const int ty = NW_STEP - 2;
+    sh.nw = p.block_warps;
+    const int ty = 2 * sh.nw - 2;
     sh.grid = dim3((p.nx + TX - 1) / TX, (p.ny + ty - 1) / ty, (p.nz + p.tile_z - 1) / p.tile_z);
-    sh.block = dim3(32, NW_STEP, 1);
-    sh.smem = StepSmem<NW_STEP>::BYTES;
+    sh.block = dim3(32, sh.nw, 1);
+    sh.smem = step_smem_bytes(sh.nw);
     return sh;
 }
 
 int max_partials(const StepParams& p, int storage) {
-    const LaunchShape sh = step_shape(p, storage);
+    StepParams q = p;
+    q.block_warps = 8;  // the smallest tile gives the most blocks
+    q.tile_z = 1;       // ... and so does the thinnest slab
+    const LaunchShape sh = step_shape(q, storage);
     const long long steps = (long long)sh.grid.x * sh.grid.y * sh.grid.z;
     const int conv = conv_blocks(p);
     return (int)(steps > conv ? steps : conv);

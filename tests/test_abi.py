@@ -47,7 +47,7 @@ def test_binding_names_match_header():
 def test_default_options():
     o = tslb.tslb_default_options()
     assert o.storage == 0 and abs(o.interface_width - 3.0) < 1e-7 and abs(o.normal_eps - 1e-2) < 1e-9
-    assert o.check_every == 0 and o.tile_z == 0 and o.graph_steps == 0
+    assert o.check_every == 0 and o.tile_z == 0 and o.graph_steps == 0 and o.block_warps == 0
 
 
 def test_workspace_bytes():

@@ -1,0 +1,115 @@
+"""Batched ensembles and the tile autotuner.
+
+Every node's arithmetic is the same in whatever tile (and launch) it is
+computed, so each grid of a batch must be bitwise equal to the same grid run
+alone, and autotuning (which only recomputes the current step into the spare
+buffer) must leave the trajectory unchanged."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2403_15773_gb300 as tslb
+from paper_2403_15773_gb300 import inputs
+from _util import oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+
+def small_ensemble():
+    ws = [
+        inputs.droplet_workload(24, radius=6.0, sigma=0.02),
+        inputs.jet_workload(32, 32, 32, diameter=6, we=300, seed=11, side="periodic"),
+        inputs.droplet_workload(40, radius=10.0, omega=1.9, sigma=0.005),
+        inputs.jet_workload(48, 36, 40, diameter=8, we=50, seed=12),
+        inputs.droplet_workload(16, radius=4.0, omega=1.2),
+        inputs.jet_workload(30, 44, 20, diameter=6, we=1000, seed=13),
+    ]
+    return ws
+
+
+def single_run(w, steps, **kw):
+    s = tslb.Simulation(w, **kw)
+    rho, u, phi = w.fields()
+    s.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    s.step(steps)
+    out = s.fields_numpy()
+    sums = s.sums()
+    s.close()
+    return out, sums
+
+
+@pytest.mark.parametrize("block_warps,tile_z", [(8, 16), (12, 32), (8, 0)])
+def test_batch_equals_each_grid_alone(block_warps, tile_z):
+    ws = small_ensemble()
+    b = tslb.BatchSimulation(ws, block_warps=block_warps, tile_z=tile_z)
+    for i, w in enumerate(ws):
+        rho, u, phi = w.fields()
+        b.set_state(i, rho, u, phi)
+    b.step(30)
+    assert b.kernel_launches == 30
+    for i, w in enumerate(ws):
+        got = b.fields_numpy(i)
+        ref, ref_sums = single_run(w, 30)
+        for k in range(4):
+            assert np.array_equal(got[k], ref[k]), (i, k)
+        # totals: each thread sums at most 64 planes in FP32 before the FP64
+        # reduction, and that grouping follows the tile shape
+        m, p = b.sums(i)
+        eps32 = 2.0 ** -24
+        assert abs(m - ref_sums[0]) <= 64 * eps32 * float(np.sum(np.abs(ref[0] - 1.0))) + 1e-9
+        assert abs(p - ref_sums[1]) <= 64 * eps32 * float(np.sum(np.abs(ref[3]))) + 1e-9
+    b.close()
+
+
+def test_batch_grid_matches_oracle():
+    ws = small_ensemble()
+    b = tslb.BatchSimulation(ws)
+    for i, w in enumerate(ws):
+        b.set_state(i, *w.fields())
+    b.step(60)
+    for i in (1, 3):
+        g = b.fields_numpy(i)
+        s = oracle_sim(ws[i])
+        s.step(60)
+        r = s.moments()
+        e_rho = np.max(np.abs(g[0] - r[0])) / np.max(np.abs(r[0]))
+        e_u = np.max(np.abs(g[1] - r[1])) / max(np.max(np.abs(r[1])), 0.05)
+        e_phi = np.max(np.abs(g[3] - r[3]))
+        assert max(e_rho, e_u, e_phi) < 1e-5, (i, e_rho, e_u, e_phi)
+    b.close()
+
+
+def test_autotune_does_not_change_the_trajectory():
+    w = inputs.jet_workload(64, 48, 80, diameter=10, seed=21)
+    ref, _ = single_run(w, 25)
+    s = tslb.Simulation(w)
+    rho, u, phi = w.fields()
+    s.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    s.step(5)
+    nw, tz = s.autotune(4)
+    assert nw in (8, 12) and tz in (16, 24, 32, 48, 64)
+    assert s.t == 5
+    s.step(20)
+    got = s.fields_numpy()
+    s.close()
+    for k in range(4):
+        assert np.array_equal(got[k], ref[k])
+
+
+def test_batch_autotune_keeps_state():
+    ws = small_ensemble()[:3]
+    a = tslb.BatchSimulation(ws)
+    b = tslb.BatchSimulation(ws)
+    for sim in (a, b):
+        for i, w in enumerate(ws):
+            sim.set_state(i, *w.fields())
+        sim.step(4)
+    a.autotune(2)
+    a.step(10)
+    b.step(10)
+    for i in range(len(ws)):
+        ga, gb = a.fields_numpy(i), b.fields_numpy(i)
+        for k in range(4):
+            assert np.array_equal(ga[k], gb[k])
+    a.close()
+    b.close()

@@ -136,11 +136,13 @@ def test_deterministic_and_graph_equals_plain_launches():
     assert sa == sb == sc
 
 
-@pytest.mark.parametrize("tile_z", [1, 5, 13])
-def test_fields_independent_of_tile_z(tile_z):
-    w = inputs.jet_workload(40, 36, 30, diameter=10, noise=0.01, seed=4)
+@pytest.mark.parametrize("tile_z,block_warps", [(1, 0), (5, 0), (13, 0), (0, 8), (0, 12), (0, 16), (7, 16)])
+def test_fields_independent_of_tiling(tile_z, block_warps):
+    """Every node's arithmetic is the same whatever tile it falls in: the fields
+    are bitwise identical for all slab depths and block shapes."""
+    w = inputs.jet_workload(70, 50, 30, diameter=10, noise=0.01, seed=4)
     a, _, _ = gpu_run(w, 12)
-    b, _, _ = gpu_run(w, 12, tile_z=tile_z)
+    b, _, _ = gpu_run(w, 12, tile_z=tile_z, block_warps=block_warps)
     for k in range(4):
         assert np.array_equal(a[k], b[k])
 

@@ -1,0 +1,82 @@
+"""Reduced-precision storage: the 11 stored fields in FP16 or BF16 (scaled
+deviations rho - 1, u, P, phi), all arithmetic in FP32.  Per-field errors
+against the FP64 oracle on a 64^3 crop of the jet (nozzle D = 8) after 1000
+steps, and against the FP32 run.
+
+Bound: the rms error of every field, on its parity scale (P: max(max|P|, U^2),
+U = 0.05, since P vanishes near rest), stays within
+16 unit roundoffs of the storage format (eps = 2^-11 for FP16, 2^-8 for BF16):
+each step re-rounds every stored value once, and the rms over the grid of
+those independent roundings grows slowly over 1000 steps.  Max errors are
+printed, not asserted: in a jet they sit on the interface, where a small shift
+of its position changes phi by O(|grad phi|)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2403_15773_gb300 as tslb
+from paper_2403_15773_gb300 import inputs
+from _util import oracle_sim
+
+pytestmark = pytest.mark.gpu
+EPS = {"fp32": 2.0 ** -24, "fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+def run(w, steps, storage):
+    rho, u, phi = w.fields()
+    s = tslb.Simulation(w, storage=storage)
+    s.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    s.step(steps)
+    out = s.fields_numpy()
+    sums = s.sums()
+    s.close()
+    return out, sums
+
+
+def field_errors(g, r):
+    # scales as in the parity tests; P, like u, can vanish, so its scale is
+    # floored at the jet's dynamic-pressure scale U^2 (U = 0.05)
+    scales = [1.0, max(np.abs(r[1]).max(), 0.05), max(np.abs(r[2]).max(), 0.05 ** 2), 1.0]
+    out = {}
+    for k, name in enumerate(("rho", "u", "P", "phi")):
+        d = np.abs(g[k] - r[k]) / scales[k]
+        out[name] = (float(d.max()), float(np.sqrt(np.mean(d * d))))
+    return out
+
+
+@pytest.fixture(scope="module")
+def crop_reference():
+    w = inputs.crop_jet(inputs.jet_workload(), 64, 64, 64, diameter=8)
+    s = oracle_sim(w)
+    s.step(1000)
+    return w, s.moments()
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_16bit_storage_error_table_vs_oracle(storage, crop_reference):
+    w, ref = crop_reference
+    g, _ = run(w, 1000, storage)
+    errs = field_errors(g, ref)
+    print(f"{storage} 64^3 jet crop, 1000 steps vs oracle: " +
+          ", ".join(f"{k} max {v[0]:.2e} rms {v[1]:.2e}" for k, v in errs.items()))
+    for name, (mx, rms) in errs.items():
+        assert np.isfinite(mx)
+        assert rms < 16 * EPS[storage], (storage, name, rms)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_16bit_storage_vs_fp32_and_conservation(storage):
+    """Against the FP32 run of the same periodic droplet; total mass and phase
+    field are still conserved to the storage rounding."""
+    w = inputs.droplet_workload(48, radius=12.0)
+    f32, s32 = run(w, 300, "fp32")
+    g, s16 = run(w, 300, storage)
+    errs = field_errors(g, f32)
+    print(f"{storage} droplet 48^3, 300 steps vs fp32: " +
+          ", ".join(f"{k} max {v[0]:.2e} rms {v[1]:.2e}" for k, v in errs.items()))
+    for name, (mx, rms) in errs.items():
+        assert rms < 16 * EPS[storage], (storage, name, rms)
+    N = w.nodes
+    # the stored totals differ from FP32's by the storage rounding of each value
+    assert abs(s16[0] - s32[0]) / N < 4 * EPS[storage] / 133.0
+    assert abs(s16[1] - s32[1]) / N < 4 * EPS[storage]
