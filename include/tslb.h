@@ -97,11 +97,12 @@ typedef struct {
                                scale * P, scale * phi; 0 = default (1/(3 U^2), 1/(2 U), 1e3, 1) */
     int32_t check_every;    /* tslb_step checks the FP64 sums for non-finite values every this
                                many steps (synchronises); 0 = never (default) */
-    int32_t tile_z;         /* z extent of one thread block's slab; 0 = automatic */
+    int32_t tile_z;         /* z extent of one thread block's slab; 0 = automatic (64 planes, fewer
+                               for grids too small to fill the GPU) */
     int32_t graph_steps;    /* steps per captured CUDA graph replayed by tslb_step; 0 = automatic,
                                1 = plain launches */
     int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 30 x 14,
-                               30 x 22, 30 x 30 interior nodes); 0 = automatic */
+                               30 x 22, 30 x 30 interior nodes); 0 = 8 */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
                                (blocking, so ordered with the legacy default stream) */
 } tslb_options;

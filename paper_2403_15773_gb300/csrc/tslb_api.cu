@@ -71,7 +71,15 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t elem_size(int storage) { return storage == TSLB_FP32 ? 4 : 2; }
 
-int auto_tile_z(int nz) { return nz < 32 ? nz : 32; }
+// Default slab depth: 64 planes, halved while the grid would give fewer than
+// two blocks per SM (small grids need the parallelism more than the fewer
+// halo planes).
+int auto_tile_z(const tslb_grid* g, int nw, int sms) {
+    const long long tiles_xy = (long long)((g->nx + 29) / 30) * ((g->ny + 2 * nw - 3) / (2 * nw - 2));
+    int tz = 64;
+    while (tz > 8 && tiles_xy * ((g->nz + tz - 1) / tz) < 2LL * sms) tz /= 2;
+    return tz < g->nz ? tz : g->nz;
+}
 
 constexpr int kAutotuneTileZ[] = {16, 24, 32, 48, 64};
 constexpr int kMinTileZ = 16;  // smallest slab the batch tile list is sized for
@@ -157,8 +165,9 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     p.ny = grid->ny;
     p.nz = grid->nz;
     for (int k = 0; k < 6; ++k) p.face[k] = b.face[k];
-    p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz) : auto_tile_z(grid->nz);
-    p.block_warps = opt->block_warps > 0 ? opt->block_warps : 12;
+    p.block_warps = opt->block_warps > 0 ? opt->block_warps : 8;
+    p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz)
+                               : auto_tile_z(grid, p.block_warps, 152);
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     p.fstride = (N + 63) / 64 * 64;
     p.omega = (float)omega;
@@ -431,7 +440,7 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
             g_init_err = count > 1 ? "grid " + std::to_string(i) + ": " + why : why;
             return TSLB_ERR_INVALID_ARG;
         }
-        if (batch) ps[i].tile_z = o.tile_z > 0 ? std::min(o.tile_z, grids[i].nz) : std::min(32, grids[i].nz);
+        if (batch) ps[i].tile_z = o.tile_z > 0 ? std::min(o.tile_z, grids[i].nz) : std::min(64, grids[i].nz);
     }
     tslb_ctx* c = new (std::nothrow) tslb_ctx();
     if (!c) {

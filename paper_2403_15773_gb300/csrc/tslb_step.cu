@@ -346,7 +346,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
 
     float sgz_cur, sgz_nxt;
     int inl_cur, inl_nxt;
-    for (int q = z0 - 2; q <= z0; ++q) {
+    for (int q = z0 - 2; q <= z0 + 1; ++q) {
         issue_phi(q);
         commit_phi(q);
     }
@@ -360,20 +360,33 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
     float2 cH = bc(0.f), cVPP = bc(0.f), cVP = bc(0.f);
     float sum_rho = 0.f, sum_phi = 0.f;
 
+    // S: what stage (d) of a plane hands to stage (e) of the same plane one
+    // iteration later (y populations kept in the thread, D3Q7 x/z terms)
+    float2 sYZ[9];
+    float sPA[9], sMB[9];
+    float2 s_hx = bc(0.f), s_vzp = bc(0.f), s_vzm = bc(0.f);
+    float s_dyA = 0.f, s_dyB = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        sYZ[k] = bc(0.f);
+        sPA[k] = sMB[k] = 0.f;
+    }
+    // the first iteration's stage (e) reads a y-exchange buffer no stage (d)
+    // has written: clear both buffers
+    for (int k = tid; k < 40 * NT; k += NT) yx[k] = 0.f;
+
     const float om1 = 1.f - P.omega, fo = 1.f - 0.5f * P.omega;
     const float sig_half = -0.5f * P.sigma;
-    int buf = 0;
-    for (int p = z0 - 1; p <= z1; ++p) {
-        issue_phi(p + 2);
-        issue_mom(p + 1, sgz_nxt, inl_nxt);
-        cp_async_commit();
-        cp_async_wait<1>();
 
-        {  // z combinations of phi at plane p
-            const float* pm = ring + ((p - 1 + 8) & 3) * NPH;
-            const float* pc = ring + ((p + 8) & 3) * NPH;
-            const float* pp = ring + ((p + 1 + 8) & 3) * NPH;
-            float* z = zc + buf * 3 * NPH;
+    // prologue: z combinations of plane z0 - 1
+    cp_async_wait<0>();
+    {
+        const int i = z0 - 2;
+        {  // z combinations of phi at plane i + 1
+            const float* pm = ring + ((i + 8) & 3) * NPH;
+            const float* pc = ring + ((i + 1 + 8) & 3) * NPH;
+            const float* pp = ring + ((i + 2 + 8) & 3) * NPH;
+            float* z = zc + ((i + 1 + 8) & 1) * 3 * NPH;
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 const int idx = tid + e * NT;
@@ -385,14 +398,118 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
                 }
             }
         }
-        __syncthreads();
 
-        float2 YZ[9];      // y populations p(0) of the (qx, c) groups
-        float PA[9], MB[9];  // p(+1) of row 2w (-> row 2w+1), p(-1) of row 2w+1 (-> row 2w)
-        float2 hx, vzp, vzm;
-        float dyA, dyB;    // D3Q7 y terms kept in the thread
+    }
+    __syncthreads();
+
+    // Software-pipelined march, one barrier per iteration i:
+    //   (c) z combinations of plane i + 1,
+    //   (e) y / z stages of plane i - 1 (output of plane i - 2),
+    //   (d) stencils, collision and x sweep of plane i.
+    // Each shared buffer (zc, yx: two each by plane parity; the phase-field
+    // ring; the moment slots) is last read one barrier before it is rewritten.
+    for (int i = z0 - 1; i <= z1 + 1; ++i) {
+        issue_phi(i + 3);
+        issue_mom(i + 1, sgz_nxt, inl_nxt);
+        cp_async_commit();
+        cp_async_wait<1>();
+
+        {  // z combinations of phi at plane i + 1
+            const float* pm = ring + ((i + 8) & 3) * NPH;
+            const float* pc = ring + ((i + 1 + 8) & 3) * NPH;
+            const float* pp = ring + ((i + 2 + 8) & 3) * NPH;
+            float* z = zc + ((i + 1 + 8) & 1) * 3 * NPH;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                const int idx = tid + e * NT;
+                if (idx < NPH) {
+                    const float a = pm[idx], b = pc[idx], c = pp[idx];
+                    z[idx] = b;
+                    z[NPH + idx] = c + a;
+                    z[2 * NPH + idx] = c - a;
+                }
+            }
+        }
+
+        // (e) plane i - 1: y shift and moments, z shift and moments, output of plane i - 2
         {
-            const float* m = mom + ((p + 8) & 1) * 10 * NS + sA;
+            const float* yprev = yx + ((i - 1 + 8) & 1) * 20 * NT + (w > 0 ? tid - 32 : tid);       // row 2w-1
+            const float* ynext = yx + ((i - 1 + 8) & 1) * 20 * NT + (w < NW - 1 ? tid + 32 : tid);  // row 2w+2
+            float2 Y[3][3][3];
+#pragma unroll
+            for (int qx = 0; qx < 3; ++qx)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int k = 3 * qx + c;
+                    const float2 qp = make_float2(yprev[(2 * k) * NT], sPA[k]);
+                    const float2 qm = make_float2(sMB[k], ynext[(2 * k + 1) * NT]);
+                    const float2 s = qp + qm;
+                    Y[qx][0][c] = s + sYZ[k];
+                    Y[qx][1][c] = qp - qm;
+                    Y[qx][2][c] = s;
+                }
+            const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], s_dyB) + make_float2(s_dyA, ynext[19 * NT]), s_hx);
+
+            const int gqx[6] = {0, 1, 0, 2, 0, 1}, gqy[6] = {0, 0, 1, 0, 2, 1};
+            float2 O0[6], O1[6], O2[6];
+#pragma unroll
+            for (int g = 0; g < 6; ++g) {
+                const Tri2 tr = pops2(Y[gqx[g]][gqy[g]][0], Y[gqx[g]][gqy[g]][1], Y[gqx[g]][gqy[g]][2]);
+                O0[g] = cPP[g] + cZ[g] + tr.m;
+                O1[g] = cPP[g] - tr.m;
+                O2[g] = cPP[g] + tr.m;
+                cPP[g] = cP[g];
+                cP[g] = tr.p;
+                cZ[g] = tr.z;
+            }
+            const float2 phin = mad(0.125f, cVPP + s_vzm, cH);
+            cH = hxy;
+            cVPP = cVP;
+            cVP = s_vzp;
+
+            if (i >= z0 + 2 && i <= z1 + 1 && (storeA || storeB)) {
+                const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
+                const float2 rn = bc(1.f) + dr, irn = rcp2(rn);
+                const float2 ux = jx * irn, uy = jy * irn, uz = jz * irn;
+                const float2 rux = rn * ux, ruy = rn * uy, ruz = rn * uz;
+                const float2 mdr = (-1.f / 3.f) * dr;
+                float2 val[NFIELDS];
+                val[F_DRHO] = dr;
+                val[F_UX] = ux;
+                val[F_UY] = uy;
+                val[F_UZ] = uz;
+                val[F_PXX] = O0[3] + mdr - rux * ux;
+                val[F_PYY] = O0[4] + mdr - ruy * uy;
+                val[F_PZZ] = O2[0] + mdr - ruz * uz;
+                val[F_PXY] = O0[5] - rux * uy;
+                val[F_PXZ] = O1[1] - rux * uz;
+                val[F_PYZ] = O1[2] - ruy * uz;
+                val[F_PHI] = phin;
+                const long long zo = nxy * (i - 2);
+                if (storeA) {
+                    S* o = out + zo + sxyA;
+#pragma unroll
+                    for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
+                    sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
+                    sum_phi += Io<S>::round_trip(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                }
+                if (storeB) {
+                    S* o = out + zo + sxyB;
+#pragma unroll
+                    for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
+                    sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
+                    sum_phi += Io<S>::round_trip(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                }
+            }
+        }
+
+        float2 nYZ[9];
+        float nPA[9], nMB[9];
+        float2 n_hx, n_vzp, n_vzm;
+        float n_dyA, n_dyB;
+        // (d) plane i: stencils, collision, x sweep, y populations -> yx[i], S
+        {
+            const float* m = mom + ((i + 8) & 1) * 10 * NS + sA;
             auto ld2 = [&](int f) { return make_float2(m[f * NS], m[f * NS + 32]); };
             const float2 sgy = make_float2(sgyA, sgyB);
             const float2 drho = ld2(0);
@@ -410,7 +527,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
 
             // grad phi and Hessian: z combos from shared memory (rows 2w-1 .. 2w+2
             // of the tile), then y combos for the row pair, then x combos
-            const float* zb = zc + buf * 3 * NPH;
+            const float* zb = zc + ((i + 8) & 1) * 3 * NPH;
             float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
@@ -520,7 +637,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
             // y populations; the row pair exchanges inside the thread, the pair
             // edges go through shared memory: p(+1) of row 2w+1 to the thread
             // below, p(-1) of row 2w to the thread above
-            float* yb = yx + buf * 20 * NT + tid;
+            float* yb = yx + ((i + 8) & 1) * 20 * NT + tid;
 #pragma unroll
             for (int qx = 0; qx < 3; ++qx)
 #pragma unroll
@@ -531,9 +648,9 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
                     const int k = 3 * qx + c;
                     yb[(2 * k) * NT] = tr.p.y;
                     yb[(2 * k + 1) * NT] = tr.m.x;
-                    YZ[k] = tr.z;
-                    PA[k] = tr.p.x;
-                    MB[k] = tr.m.y;
+                    nYZ[k] = tr.z;
+                    nPA[k] = tr.p.x;
+                    nMB[k] = tr.m.y;
                 }
 
             // D3Q7: g_i^post = w_i (B0 + c_i . B1)
@@ -543,92 +660,31 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
             const float2 b1y = mad(fphi, vy, ga * nyv);
             const float2 b1z = mad(fphi, vz, ga * nzv);
             const float2 fromL = shfl_up2(phi + b1x), fromR = shfl_down2(phi - b1x);
-            hx = mad(0.25f, phi, 0.125f * (fromL + fromR));
+            n_hx = mad(0.25f, phi, 0.125f * (fromL + fromR));
             const float2 yp = phi + b1y, ym = phi - b1y;
             yb[18 * NT] = yp.y;
             yb[19 * NT] = ym.x;
-            dyA = ym.y;  // row 2w+1 -> row 2w
-            dyB = yp.x;  // row 2w -> row 2w+1
-            vzp = phi + b1z;
-            vzm = phi - b1z;
+            n_dyA = ym.y;  // row 2w+1 -> row 2w
+            n_dyB = yp.x;  // row 2w -> row 2w+1
+            n_vzp = phi + b1z;
+            n_vzm = phi - b1z;
         }
         __syncthreads();
-
-        {
-            const float* yprev = yx + buf * 20 * NT + (w > 0 ? tid - 32 : tid);       // row 2w-1
-            const float* ynext = yx + buf * 20 * NT + (w < NW - 1 ? tid + 32 : tid);  // row 2w+2
-            float2 Y[3][3][3];
+        commit_phi(i + 3);
+        commit_mom(i + 1);
 #pragma unroll
-            for (int qx = 0; qx < 3; ++qx)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int k = 3 * qx + c;
-                    const float2 qp = make_float2(yprev[(2 * k) * NT], PA[k]);
-                    const float2 qm = make_float2(MB[k], ynext[(2 * k + 1) * NT]);
-                    const float2 s = qp + qm;
-                    Y[qx][0][c] = s + YZ[k];
-                    Y[qx][1][c] = qp - qm;
-                    Y[qx][2][c] = s;
-                }
-            const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], dyB) + make_float2(dyA, ynext[19 * NT]), hx);
-
-            const int gqx[6] = {0, 1, 0, 2, 0, 1}, gqy[6] = {0, 0, 1, 0, 2, 1};
-            float2 O0[6], O1[6], O2[6];
-#pragma unroll
-            for (int g = 0; g < 6; ++g) {
-                const Tri2 tr = pops2(Y[gqx[g]][gqy[g]][0], Y[gqx[g]][gqy[g]][1], Y[gqx[g]][gqy[g]][2]);
-                O0[g] = cPP[g] + cZ[g] + tr.m;
-                O1[g] = cPP[g] - tr.m;
-                O2[g] = cPP[g] + tr.m;
-                cPP[g] = cP[g];
-                cP[g] = tr.p;
-                cZ[g] = tr.z;
-            }
-            const float2 phin = mad(0.125f, cVPP + vzm, cH);
-            cH = hxy;
-            cVPP = cVP;
-            cVP = vzp;
-
-            if (p >= z0 + 1 && (storeA || storeB)) {
-                const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
-                const float2 rn = bc(1.f) + dr, irn = rcp2(rn);
-                const float2 ux = jx * irn, uy = jy * irn, uz = jz * irn;
-                const float2 rux = rn * ux, ruy = rn * uy, ruz = rn * uz;
-                const float2 mdr = (-1.f / 3.f) * dr;
-                float2 val[NFIELDS];
-                val[F_DRHO] = dr;
-                val[F_UX] = ux;
-                val[F_UY] = uy;
-                val[F_UZ] = uz;
-                val[F_PXX] = O0[3] + mdr - rux * ux;
-                val[F_PYY] = O0[4] + mdr - ruy * uy;
-                val[F_PZZ] = O2[0] + mdr - ruz * uz;
-                val[F_PXY] = O0[5] - rux * uy;
-                val[F_PXZ] = O1[1] - rux * uz;
-                val[F_PYZ] = O1[2] - ruy * uz;
-                val[F_PHI] = phin;
-                const long long zo = nxy * (p - 1);
-                if (storeA) {
-                    S* o = out + zo + sxyA;
-#pragma unroll
-                    for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
-                    sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                    sum_phi += Io<S>::round_trip(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
-                }
-                if (storeB) {
-                    S* o = out + zo + sxyB;
-#pragma unroll
-                    for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
-                    sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                    sum_phi += Io<S>::round_trip(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
-                }
-            }
+        for (int k = 0; k < 9; ++k) {
+            sYZ[k] = nYZ[k];
+            sPA[k] = nPA[k];
+            sMB[k] = nMB[k];
         }
-        commit_phi(p + 2);
-        commit_mom(p + 1);
+        s_hx = n_hx;
+        s_vzp = n_vzp;
+        s_vzm = n_vzm;
+        s_dyA = n_dyA;
+        s_dyB = n_dyB;
         sgz_cur = sgz_nxt;
         inl_cur = inl_nxt;
-        buf ^= 1;
     }
     cp_async_wait<0>();
 
