@@ -183,6 +183,23 @@ def cpu_baseline(w, budget_s: float = 12.0):
                       f"{dt:.1f} s"}
 
 
+# ------------------------------------------------------------- multi-rank
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest `value` over all ranks (every rank gets it)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(nodes_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Lattice updates of all ranks over the slowest rank's time, in GLUPS."""
+    return nodes_per_rank * world * steps / (ms_max * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def run_gpu(args, w, storage: str, rank: int, world: int, dist):
@@ -219,11 +236,7 @@ def run_gpu(args, w, storage: str, rank: int, world: int, dist):
     launches = sim.kernel_launches - launches0
     m, p = sim.sums()
     ok = math.isfinite(m) and math.isfinite(p)
-    # max over ranks of the device time
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)  # the slowest rank sets the job's time
     sim.close()
     return {"ms": ms, "launches": launches, "clocks": sampler.summary(), "finite": ok,
             "shape": {"block_warps": shape[0], "tile_z": shape[1]} if shape else
@@ -281,7 +294,7 @@ def run_batched(args):
                         "and jets (D = 0.15 edge, periodic sides), We log-uniform in [10, 2000], seed 4"}
 
 
-def run_e2e(args, w, storage: str):
+def run_e2e(args, w, storage: str, world: int = 1, dist=None):
     """Same metric through the public C ABI with host buffers: upload the
     initial fields from pinned memory, run the steps, read the moments, the
     phase field and the FP64 sums back into pinned memory."""
@@ -301,6 +314,8 @@ def run_e2e(args, w, storage: str):
     sim.moments_host(out_rho, out_u, out_pi)
     sim.phi_host(out_phi)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     sim.set_state_host(rho, u, phi)
     sim.step(args.steps)
@@ -309,9 +324,10 @@ def run_e2e(args, w, storage: str):
     m, p = sim.sums()
     dt = time.perf_counter() - t0
     sim.close()
+    dt = max_over_ranks(dt * 1e3, dist, torch.device("cuda", torch.cuda.current_device())) * 1e-3
     h2d = 5 * N * 4
     d2h = 11 * N * 4 + 16
-    return {"value": N * args.steps / dt / 1e9, "unit": UNIT,
+    return {"value": whole_job_rate(N, world, args.steps, dt * 1e3), "unit": UNIT,
             "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
             "note": "one job per timed region: set_state from pinned host buffers, the steps, "
                     "get_moments + get_phi into pinned host buffers, FP64 sums; bytes per step "
@@ -410,7 +426,7 @@ def main():
         errs, err_case = oracle_errors(w, [args.storage] + vlist)
         for v in vlist:
             variants[v]["oracle_err"] = errs[v]
-    e2e = None if args.no_e2e else run_e2e(args, w, args.storage)
+    e2e = None if args.no_e2e else run_e2e(args, w, args.storage, world, dist)
     if dist is not None:
         dist.barrier()
     if rank != 0:
@@ -418,9 +434,8 @@ def main():
             dist.destroy_process_group()
         return
 
-    nodes_total = w.nodes * world
     sec = res["ms"] * 1e-3
-    glups = nodes_total * args.steps / sec / 1e9
+    glups = whole_job_rate(w.nodes, world, args.steps, res["ms"])
     bpn = FIELDS * 2 * (4 if args.storage == "fp32" else 2)
     per_launch = sec / args.steps
     peak, peak_kind = measured_peaks()
