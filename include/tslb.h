@@ -103,6 +103,9 @@ typedef struct {
                                1 = plain launches */
     int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 30 x 14,
                                30 x 22, 30 x 30 interior nodes); 0 = 8 */
+    int32_t average;        /* 1: every step also adds the new phi and u_z of each node to FP64
+                               time sums (the time-averaged fields of Sec. 3: centre-line and
+                               radial profiles of <phi> and <u_z>); 0 = off (default) */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
                                (blocking, so ordered with the legacy default stream) */
 } tslb_options;
@@ -199,6 +202,14 @@ TSLB_API tslb_status tslb_batch_get_moments(tslb_ctx* ctx, int32_t instance, flo
 TSLB_API tslb_status tslb_batch_get_phi(tslb_ctx* ctx, int32_t instance, float* phi, int on_device);
 TSLB_API tslb_status tslb_batch_sums(tslb_ctx* ctx, int32_t instance, double* mass, double* phi_total);
 TSLB_API int32_t tslb_batch_count(const tslb_ctx* ctx);
+
+/* Time sums of phi and u_z (option `average`), N doubles each (either may be
+ * NULL), accumulated over the *steps steps taken since the state was set or
+ * the sums were reset; the time averages are sum / steps.  Autotuner trials
+ * are not counted. */
+TSLB_API tslb_status tslb_get_averages(tslb_ctx* ctx, int32_t instance, double* phi_sum, double* uz_sum,
+                                       int64_t* steps, int on_device);
+TSLB_API tslb_status tslb_reset_averages(tslb_ctx* ctx);
 
 /* Tile-shape autotuner: times the step kernel for blocks of 8 and 12 warps
  * and z slabs of 16, 24, 32, 48 and 64 planes (steps_per_trial launches

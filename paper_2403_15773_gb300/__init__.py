@@ -29,7 +29,7 @@ __all__ = [
     "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
     "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
     "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
-    "Simulation", "BatchSimulation", "SYMBOLS",
+    "tslb_get_averages", "tslb_reset_averages", "Simulation", "BatchSimulation", "SYMBOLS",
 ]
 
 TSLB_OK, TSLB_ERR_INVALID_ARG, TSLB_ERR_OOM, TSLB_ERR_CUDA, TSLB_ERR_UNSTABLE, TSLB_ERR_TIMEOUT, \
@@ -43,7 +43,8 @@ SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_se
            "tslb_get_state", "tslb_put_state", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
            "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
            "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
-           "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune")
+           "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
+           "tslb_get_averages", "tslb_reset_averages")
 
 
 class Grid(ctypes.Structure):
@@ -61,7 +62,7 @@ class Options(ctypes.Structure):
                 ("normal_eps", ctypes.c_float), ("field_scale", ctypes.c_float * 4),
                 ("check_every", ctypes.c_int32), ("tile_z", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("block_warps", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("average", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
 class TslbError(RuntimeError):
@@ -123,6 +124,10 @@ def lib() -> ctypes.CDLL:
             L.tslb_batch_count.argtypes = [VP]
             L.tslb_batch_count.restype = ctypes.c_int32
             L.tslb_autotune.argtypes = [VP, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]
+            L.tslb_get_averages.argtypes = [VP, ctypes.c_int32, VP, VP, P(ctypes.c_int64), ctypes.c_int]
+            L.tslb_get_averages.restype = ctypes.c_int
+            L.tslb_reset_averages.argtypes = [VP]
+            L.tslb_reset_averages.restype = ctypes.c_int
             for name in ("tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments", "tslb_batch_get_phi",
                          "tslb_batch_sums", "tslb_autotune"):
                 getattr(L, name).restype = ctypes.c_int
@@ -278,6 +283,17 @@ def tslb_autotune(ctx: int, steps_per_trial: int = 8):
     return nw.value, tz.value
 
 
+def tslb_get_averages(ctx: int, i: int, phi_sum: int, uz_sum: int, on_device: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().tslb_get_averages(ctx, int(i), phi_sum or None, uz_sum or None, ctypes.byref(n), int(on_device)),
+           ctx)
+    return n.value
+
+
+def tslb_reset_averages(ctx: int):
+    _check(lib().tslb_reset_averages(ctx), ctx)
+
+
 # ------------------------------------------------------------ convenience
 
 def _boundary_from(workload) -> Boundary:
@@ -303,7 +319,8 @@ class Simulation:
     """
 
     def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
-                 graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0):
+                 graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0,
+                 average: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Simulation needs a CUDA device")
@@ -319,6 +336,7 @@ class Simulation:
         o.graph_steps = int(graph_steps)
         o.check_every = int(check_every)
         o.block_warps = int(block_warps)
+        o.average = 1 if average else 0
         if field_scale is not None:
             for g in range(4):
                 o.field_scale[g] = float(field_scale[g])
@@ -423,6 +441,21 @@ class Simulation:
     def autotune(self, steps_per_trial: int = 8):
         """Pick the fastest block shape and slab depth; the state is unchanged."""
         return tslb_autotune(self.ctx, steps_per_trial)
+
+    def averages(self):
+        """Time averages (<phi>, <u_z>) as float64 numpy arrays shaped like the
+        grid, and the number of steps they cover (needs average=True)."""
+        import torch
+        w = self.workload
+        a = torch.empty(2 * self.N, dtype=torch.float64, device="cuda")
+        n = tslb_get_averages(self.ctx, 0, a.data_ptr(), a.data_ptr() + 8 * self.N, 1)
+        s = (w.nz, w.ny, w.nx)
+        a = a.cpu().numpy()
+        k = max(n, 1)
+        return a[:self.N].reshape(s) / k, a[self.N:].reshape(s) / k, n
+
+    def reset_averages(self):
+        tslb_reset_averages(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -24,6 +24,7 @@ struct Instance {
     StepParams p;
     long long N = 0;
     void* buf[2] = {nullptr, nullptr};
+    double* avg = nullptr;  // time sums of phi and u_z (option `average`)
     int tile_begin = 0, tile_end = 0;  // batch: its tiles in the tile list
     bool set = false;
 };
@@ -60,6 +61,8 @@ struct tslb_ctx {
     int check_every = 0;
     int64_t since_check = 0;
     int64_t launches = 0;
+    bool average = false;
+    int64_t avg_steps = 0;
     std::string err;
 };
 
@@ -240,12 +243,12 @@ int tiles_of(const StepParams& p, int nw, int tile_z) {
 // pair, the two-slot step counter, the two batch tile counters, and for a
 // batch the device copy of the instances and the tile list.
 struct Layout {
-    std::vector<size_t> state;
+    std::vector<size_t> state, avg;
     size_t staging, partials, result, tdev, counters, dinst, dtiles, total;
     int max_tiles, max_conv;
 };
 
-Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, bool batch) {
+Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, bool batch, bool average) {
     Layout L;
     size_t off = 0;
     long long maxf = 0;
@@ -253,6 +256,8 @@ Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, b
     for (const StepParams& p : ps) {
         L.state.push_back(off);
         off += 2 * align256(tslb::NFIELDS * (size_t)p.fstride * elem);
+        L.avg.push_back(off);
+        if (average) off += align256(2 * (size_t)p.fstride * sizeof(double));
         maxf = std::max(maxf, p.fstride);
         if (batch)
             tiles += tiles_of(p, 8, std::min(p.tile_z, kMinTileZ));
@@ -481,7 +486,8 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
         }
         c->own_stream = true;
     }
-    const Layout L = layout_for(ps, c->elem, c->storage, batch);
+    c->average = o.average != 0;
+    const Layout L = layout_for(ps, c->elem, c->storage, batch, c->average);
     if (workspace) {
         if (workspace_bytes < L.total) {
             c->err = "workspace smaller than the workspace-bytes query";
@@ -512,6 +518,10 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
         I.N = (long long)grids[i].nx * grids[i].ny * grids[i].nz;
         I.buf[0] = base + L.state[i];
         I.buf[1] = base + L.state[i] + align256(tslb::NFIELDS * (size_t)ps[i].fstride * c->elem);
+        if (c->average) {
+            I.avg = reinterpret_cast<double*>(base + L.avg[i]);
+            I.p.avg = I.avg;
+        }
     }
     c->staging = reinterpret_cast<float*>(base + L.staging);
     c->partials = reinterpret_cast<double*>(base + L.partials);
@@ -557,6 +567,10 @@ tslb_status set_state_of(tslb_ctx* c, int i, const float* rho, const float* u, c
            "zero P");
     }
     if ((s = put_field(c, I, phi, tslb::F_PHI, on_device)) != TSLB_OK) return s;
+    if (I.avg) {
+        CK(cudaMemsetAsync(I.avg, 0, 2 * (size_t)I.p.fstride * sizeof(double), c->stream), "clear averages");
+        c->avg_steps = 0;
+    }
     // the step index restarts with every state that is set
     long long tt[2] = {0, 0};
     CK(cudaMemcpyAsync(c->tdev, tt, sizeof(tt), cudaMemcpyHostToDevice, c->stream), "step counter");
@@ -641,7 +655,7 @@ size_t tslb_batch_workspace_bytes(int32_t count, const tslb_grid* grids, const t
         // the face rules only affect validity, not the size: size with periodic faces
         if (!make_params(&grids[i], 1.0, 0.0, &b, &o, ps[i], why)) return 0;
     }
-    return layout_for(ps, elem_size(o.storage), o.storage, count > 1).total;
+    return layout_for(ps, elem_size(o.storage), o.storage, count > 1, o.average != 0).total;
 }
 
 tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattice, double omega, double sigma,
@@ -703,6 +717,7 @@ tslb_status tslb_step(tslb_ctx* c, int64_t n) {
         }
         // graphs hold an even number of steps, so only plain launches flip cur
         c->t += chunk;
+        if (c->average) c->avg_steps += chunk;
         n -= chunk;
         c->parts_valid = true;
         if (c->check_every > 0) {
@@ -779,6 +794,8 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     CK(cudaEventCreate(&e1), "event create");
     std::vector<int> keep_tz(c->inst.size());
     for (size_t i = 0; i < c->inst.size(); ++i) keep_tz[i] = c->inst[i].p.tile_z;
+    // the trial steps must not add to the time sums
+    for (Instance& I : c->inst) I.p.avg = nullptr;
     float best = 1e30f;
     int best_nw = c->batch ? c->batch_nw : c->inst[0].p.block_warps, best_tz = keep_tz[0];
     tslb_status st = TSLB_OK;
@@ -816,6 +833,7 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     // apply the winner (or restore on failure)
     for (size_t i = 0; i < c->inst.size(); ++i) {
         Instance& I = c->inst[i];
+        I.p.avg = I.avg;
         I.p.block_warps = best_nw;
         I.p.tile_z = st == TSLB_OK ? std::min(best_tz, I.p.nz) : keep_tz[i];
     }
@@ -936,5 +954,35 @@ const char* tslb_status_string(tslb_status s) {
 int64_t tslb_kernel_launches(const tslb_ctx* c) { return c ? c->launches : 0; }
 
 int32_t tslb_batch_count(const tslb_ctx* c) { return c ? (int32_t)c->inst.size() : 0; }
+
+tslb_status tslb_get_averages(tslb_ctx* c, int32_t instance, double* phi_sum, double* uz_sum, int64_t* steps,
+                              int on_device) {
+    if (!c) return TSLB_ERR_INVALID_ARG;
+    tslb_status s = check_instance(c, instance);
+    if (s != TSLB_OK) return s;
+    if (!c->average) return bad(c, "the context was created without the average option", TSLB_ERR_STATE);
+    if (on_device && ((phi_sum && !is_device_ptr(phi_sum)) || (uz_sum && !is_device_ptr(uz_sum))))
+        return bad(c, "on_device pointers must be device memory");
+    CK(cudaSetDevice(c->device), "set device");
+    Instance& I = c->inst[instance];
+    const size_t bytes = (size_t)I.N * sizeof(double);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (phi_sum) CK(cudaMemcpyAsync(phi_sum, I.avg, bytes, kind, c->stream), "averages copy");
+    if (uz_sum) CK(cudaMemcpyAsync(uz_sum, I.avg + I.p.fstride, bytes, kind, c->stream), "averages copy");
+    CK(cudaStreamSynchronize(c->stream), "averages synchronise");
+    if (steps) *steps = c->avg_steps;
+    return TSLB_OK;
+}
+
+tslb_status tslb_reset_averages(tslb_ctx* c) {
+    if (!c) return TSLB_ERR_INVALID_ARG;
+    if (!c->average) return bad(c, "the context was created without the average option", TSLB_ERR_STATE);
+    CK(cudaSetDevice(c->device), "set device");
+    for (Instance& I : c->inst)
+        CK(cudaMemsetAsync(I.avg, 0, 2 * (size_t)I.p.fstride * sizeof(double), c->stream), "clear averages");
+    CK(cudaStreamSynchronize(c->stream), "averages synchronise");
+    c->avg_steps = 0;
+    return TSLB_OK;
+}
 
 }  // extern "C"

@@ -28,6 +28,7 @@ struct StepParams {
     unsigned seed_lo, seed_hi;
     float scale[NFIELDS];    // 16-bit storage: stored = scale * value
     float inv_scale[NFIELDS];
+    double* avg;             // time sums of phi and u_z (2 blocks of fstride doubles) or null
 };
 
 // One grid of a batch: its parameters and its two state buffers.

@@ -500,6 +500,18 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
                     sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
                     sum_phi += Io<S>::round_trip(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
+                if (P.avg) {  // time sums of the new phi and u_z (FP64)
+                    if (storeA) {
+                        double* a = P.avg + zo + sxyA;
+                        a[0] += (double)phin.x;
+                        a[fs] += (double)uz.x;
+                    }
+                    if (storeB) {
+                        double* a = P.avg + zo + sxyB;
+                        a[0] += (double)phin.y;
+                        a[fs] += (double)uz.y;
+                    }
+                }
             }
         }
 

@@ -236,3 +236,73 @@ def test_full_size_jet_sampled_step():
     assert max(e_rho, e_u, e_phi) < TOL, (e_rho, e_u, e_phi)
     e_pi = np.max(np.abs(g_pi[:, idx].T - out[:, 4:10])) / max(np.max(np.abs(out[:, 4:10])), 1e-8)
     assert e_pi < 1e-3, e_pi
+
+
+@pytest.mark.parametrize("we", [10.0, 2000.0])
+def test_weber_sweep_512_sampled_step(we):
+    """The 512 x 512 x 1024 jet of the Weber sweep (D = 40, Re = 5000,
+    268 M nodes, 23.6 GB of FP32 state) in the default launch configuration:
+    after 20 steps, one more step checked at 3000 sampled nodes (boundary
+    faces, the nozzle rim and the interior) against the oracle's single-step
+    evaluation from the same stored state."""
+    w = [x for x in inputs.weber_sweep() if x.sigma == pytest.approx(0.05 ** 2 * 40 / we)][0]
+    rho, u, phi = w.fields()
+    sim = tslb.Simulation(w)
+    sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    del rho, u, phi
+    sim.step(20)
+    before = sim.fields_numpy()
+    t = sim.t
+    sim.step(1)
+    nx, ny, nz = w.nx, w.ny, w.nz
+    rng = np.random.default_rng(1)
+    pts = [rng.integers(0, [nx, ny, nz], size=(1500, 3))]
+    for axis, val in ((0, 0), (0, nx - 1), (1, 0), (1, ny - 1), (2, 0), (2, nz - 1)):
+        p = rng.integers(0, [nx, ny, nz], size=(150, 3))
+        p[:, axis] = val
+        pts.append(p)
+    ang = rng.uniform(0, 2 * np.pi, 300)
+    rim = np.stack([np.round(256 + 20 * np.cos(ang)), np.round(256 + 20 * np.sin(ang)),
+                    rng.integers(0, 4, 300)], 1).astype(np.int64)
+    pts.append(rim)
+    P = np.concatenate(pts)
+    idx = P[:, 0] + nx * (P[:, 1] + ny * P[:, 2])
+    flat = lambda a: a.reshape(a.shape[0], -1) if a.ndim == 4 else a.reshape(-1)
+    out = oracle.step_sample(oracle_params(w), t, flat(before[0]), flat(before[1]), flat(before[2]),
+                             flat(before[3]), idx)
+    del before
+    after = sim.fields_numpy()
+    sim.close()
+    g_rho, g_u, g_pi, g_phi = (flat(a) for a in after)
+    e_rho = np.max(np.abs(g_rho[idx] - out[:, 0])) / np.max(np.abs(out[:, 0]))
+    e_u = np.max(np.abs(g_u[:, idx].T - out[:, 1:4])) / max(np.max(np.abs(out[:, 1:4])), 0.05)
+    e_phi = np.max(np.abs(g_phi[idx] - out[:, 10]))
+    print(f"parity 512x512x1024 We {we:g} sampled step: err rho {e_rho:.2e} u {e_u:.2e} phi {e_phi:.2e}")
+    assert max(e_rho, e_u, e_phi) < TOL, (e_rho, e_u, e_phi)
+
+
+def test_time_averages_match_oracle():
+    """The fused FP64 time sums of phi and u_z equal the oracle's per-step
+    fields summed over the same steps; autotuner trials add nothing."""
+    w = inputs.jet_workload(48, 40, 44, diameter=12, we=100, noise=0.01, seed=3)
+    rho, u, phi = w.fields()
+    sim = tslb.Simulation(w, average=True)
+    sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    sim.step(10)
+    sim.autotune(2)
+    sim.step(50)
+    avg_phi, avg_uz, n = sim.averages()
+    sim.close()
+    assert n == 60
+    s = oracle_sim(w)
+    acc_phi = np.zeros_like(phi)
+    acc_uz = np.zeros_like(phi)
+    for _ in range(60):
+        s.step(1)
+        _, uu, _, ph = s.moments()
+        acc_phi += ph
+        acc_uz += uu[2]
+    e_phi = np.max(np.abs(avg_phi - acc_phi / 60))
+    e_uz = np.max(np.abs(avg_uz - acc_uz / 60)) / max(np.max(np.abs(acc_uz / 60)), 0.05)
+    print(f"parity time averages 60 steps: phi {e_phi:.2e} u_z {e_uz:.2e}")
+    assert max(e_phi, e_uz) < TOL

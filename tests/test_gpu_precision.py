@@ -80,3 +80,18 @@ def test_16bit_storage_vs_fp32_and_conservation(storage):
     # the stored totals differ from FP32's by the storage rounding of each value
     assert abs(s16[0] - s32[0]) / N < 4 * EPS[storage] / 133.0
     assert abs(s16[1] - s32[1]) / N < 4 * EPS[storage]
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_16bit_storage_full_jet_vs_fp32(storage):
+    """The 192 x 192 x 384 jet with 16-bit storage against the FP32 run after
+    500 steps: per-field max and L2 (rms) errors on the parity scales."""
+    w = inputs.jet_workload()
+    f32, _ = run(w, 500, "fp32")
+    g, _ = run(w, 500, storage)
+    errs = field_errors(g, f32)
+    print(f"{storage} jet 192x192x384, 500 steps vs fp32: " +
+          ", ".join(f"{k} max {v[0]:.2e} rms {v[1]:.2e}" for k, v in errs.items()))
+    for name, (mx, rms) in errs.items():
+        assert np.isfinite(mx)
+        assert rms < 16 * EPS[storage], (storage, name, rms)
