@@ -306,3 +306,26 @@ def test_time_averages_match_oracle():
     e_uz = np.max(np.abs(avg_uz - acc_uz / 60)) / max(np.max(np.abs(acc_uz / 60)), 0.05)
     print(f"parity time averages 60 steps: phi {e_phi:.2e} u_z {e_uz:.2e}")
     assert max(e_phi, e_uz) < TOL
+
+
+def test_non_finite_state_is_reported():
+    """Failure detection without any GPU fault: a NaN planted in the initial
+    density on the host propagates through plain arithmetic, and the FP64
+    totals checked every `check_every` steps turn it into TSLB_ERR_UNSTABLE."""
+    w = inputs.droplet_workload(24)
+    rho, u, phi = w.fields()
+    rho = rho.copy()
+    rho[12, 12, 12] = np.nan
+    sim = tslb.Simulation(w, check_every=5)
+    sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    with pytest.raises(tslb.TslbError) as ei:
+        sim.step(20)
+    assert ei.value.status == tslb.TSLB_ERR_UNSTABLE
+    assert "finite" in str(ei.value)
+    sim.close()
+    # a healthy run with the same checks passes
+    s2 = tslb.Simulation(w, check_every=5)
+    s2.set_state(*(torch.from_numpy(a) for a in w.fields()))
+    s2.step(20)
+    assert s2.t == 20
+    s2.close()
