@@ -103,6 +103,10 @@ typedef struct {
                                1 = plain launches */
     int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 30 x 14,
                                30 x 22, 30 x 30 interior nodes); 0 = 8 */
+    int32_t scheme;         /* 0: the fused moment-only step (default, 88 B per update in FP32);
+                               1: the paper's two-sweep design kept as an ablation: collide+push
+                               into 34 population arrays in HBM, then their moments (360 B per
+                               update; single grid, FP32, no averages, no autotune) */
     int32_t average;        /* 1: every step also adds the new phi and u_z of each node to FP64
                                time sums (the time-averaged fields of Sec. 3: centre-line and
                                radial profiles of <phi> and <u_z>); 0 = off (default) */

@@ -62,7 +62,7 @@ class Options(ctypes.Structure):
                 ("normal_eps", ctypes.c_float), ("field_scale", ctypes.c_float * 4),
                 ("check_every", ctypes.c_int32), ("tile_z", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("block_warps", ctypes.c_int32),
-                ("average", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("scheme", ctypes.c_int32), ("average", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
 class TslbError(RuntimeError):
@@ -320,7 +320,7 @@ class Simulation:
 
     def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
                  graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0,
-                 average: bool = False):
+                 average: bool = False, scheme: str = "fused"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Simulation needs a CUDA device")
@@ -337,6 +337,7 @@ class Simulation:
         o.check_every = int(check_every)
         o.block_warps = int(block_warps)
         o.average = 1 if average else 0
+        o.scheme = {"fused": 0, "two_sweep": 1}[scheme]
         if field_scale is not None:
             for g in range(4):
                 o.field_scale[g] = float(field_scale[g])

@@ -63,6 +63,8 @@ struct tslb_ctx {
     int64_t launches = 0;
     bool average = false;
     int64_t avg_steps = 0;
+    int scheme = 0;          // 0 fused moment-only step, 1 the paper's two-sweep design
+    float* pops = nullptr;   // scheme 1: 34 population arrays
     std::string err;
 };
 
@@ -244,11 +246,12 @@ int tiles_of(const StepParams& p, int nw, int tile_z) {
 // batch the device copy of the instances and the tile list.
 struct Layout {
     std::vector<size_t> state, avg;
-    size_t staging, partials, result, tdev, counters, dinst, dtiles, total;
+    size_t staging, partials, result, tdev, counters, dinst, dtiles, pops, total;
     int max_tiles, max_conv;
 };
 
-Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, bool batch, bool average) {
+Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, bool batch, bool average,
+                  int scheme = 0) {
     Layout L;
     size_t off = 0;
     long long maxf = 0;
@@ -264,6 +267,7 @@ Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, b
         else
             tiles = std::max(tiles, tslb::max_partials(p, storage));
         conv = std::max(conv, tslb::max_partials(p, storage));
+        if (scheme == 1) conv = std::max(conv, tslb::twosweep_partials(p));
     }
     L.max_tiles = tiles;
     L.max_conv = conv;
@@ -281,6 +285,8 @@ Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, b
     off += batch ? align256(ps.size() * sizeof(tslb::BatchInstance)) : 0;
     L.dtiles = off;
     off += batch ? align256((size_t)tiles * sizeof(int4)) : 0;
+    L.pops = off;
+    if (scheme == 1) off += align256(34 * (size_t)ps[0].fstride * sizeof(float));
     L.total = off;
     return L;
 }
@@ -335,6 +341,11 @@ tslb_status upload_batch(tslb_ctx* c) {
 
 // One time step from parity q (state buf[q], step counter tdev[q]) to q ^ 1.
 cudaError_t launch_one(tslb_ctx* c, int q) {
+    if (c->scheme == 1) {
+        Instance& I = c->inst[0];
+        return tslb::launch_twosweep_step(I.p, static_cast<float*>(I.buf[0]), c->pops, c->tdev + q,
+                                          c->tdev + (q ^ 1), c->partials, c->stream);
+    }
     if (!c->batch) {
         Instance& I = c->inst[0];
         return tslb::launch_step(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
@@ -386,6 +397,8 @@ tslb_status finish_sums(tslb_ctx* c, int i, double* mass, double* phi_total) {
         if (c->batch) {
             parts = c->partials + 2 * (size_t)I.tile_begin;
             n = I.tile_end - I.tile_begin;
+        } else if (c->scheme == 1) {
+            n = tslb::twosweep_partials(I.p);
         } else {
             n = tiles_of(I.p, I.p.block_warps, I.p.tile_z);
         }
@@ -438,6 +451,14 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
         g_init_err = "batches use blocks of 8 or 12 warps";
         return TSLB_ERR_INVALID_ARG;
     }
+    if (o.scheme != 0 && o.scheme != 1) {
+        g_init_err = "scheme must be 0 (fused) or 1 (two sweeps)";
+        return TSLB_ERR_INVALID_ARG;
+    }
+    if (o.scheme == 1 && (batch || o.storage != TSLB_FP32 || o.average)) {
+        g_init_err = "the two-sweep scheme runs single grids in FP32 without averages";
+        return TSLB_ERR_INVALID_ARG;
+    }
     std::vector<StepParams> ps(count);
     for (int i = 0; i < count; ++i) {
         std::string why;
@@ -487,7 +508,8 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
         c->own_stream = true;
     }
     c->average = o.average != 0;
-    const Layout L = layout_for(ps, c->elem, c->storage, batch, c->average);
+    c->scheme = o.scheme;
+    const Layout L = layout_for(ps, c->elem, c->storage, batch, c->average, c->scheme);
     if (workspace) {
         if (workspace_bytes < L.total) {
             c->err = "workspace smaller than the workspace-bytes query";
@@ -531,6 +553,10 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
     c->counters = reinterpret_cast<int*>(base + L.counters);
     c->dinst = reinterpret_cast<tslb::BatchInstance*>(base + L.dinst);
     c->dtiles = reinterpret_cast<int4*>(base + L.dtiles);
+    if (c->scheme == 1) {
+        c->pops = reinterpret_cast<float*>(base + L.pops);
+        c->inst[0].buf[1] = c->inst[0].buf[0];  // the moments are updated in place
+    }
     e = cudaMemsetAsync(c->counters, 0, 256, c->stream);
     if (e != cudaSuccess) {
         c->err = std::string("counter reset: ") + cudaGetErrorString(e);
@@ -655,7 +681,7 @@ size_t tslb_batch_workspace_bytes(int32_t count, const tslb_grid* grids, const t
         // the face rules only affect validity, not the size: size with periodic faces
         if (!make_params(&grids[i], 1.0, 0.0, &b, &o, ps[i], why)) return 0;
     }
-    return layout_for(ps, elem_size(o.storage), o.storage, count > 1, o.average != 0).total;
+    return layout_for(ps, elem_size(o.storage), o.storage, count > 1, o.average != 0, o.scheme).total;
 }
 
 tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattice, double omega, double sigma,
@@ -784,6 +810,7 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     if (!c) return TSLB_ERR_INVALID_ARG;
     if (steps_per_trial < 1) return bad(c, "steps_per_trial must be >= 1");
     if (!all_set(c)) return bad(c, "tslb_autotune before the state of every grid is set", TSLB_ERR_STATE);
+    if (c->scheme == 1) return bad(c, "the two-sweep scheme has no tile shape to tune");
     CK(cudaSetDevice(c->device), "set device");
     const int q = c->cur;
     const int warps_single[] = {8, 12};

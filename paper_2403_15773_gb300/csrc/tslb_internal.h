@@ -81,6 +81,13 @@ cudaError_t launch_batch_step(int nw, const BatchInstance* insts, const int4* ti
                               const long long* t_in, long long* t_out, int* counters, double* partials,
                               int nblocks, cudaStream_t s);
 
+// The paper's two-sweep design (ablation): collide+push of the moments M into
+// 34 population arrays `pops` (27 f_i - w_i, then 7 g_k), then the moments of
+// the populations back into M (in place) with block partial sums.
+int twosweep_partials(const StepParams& p);
+cudaError_t launch_twosweep_step(const StepParams& p, float* M, float* pops, const long long* t_in,
+                                 long long* t_out, double* partials, cudaStream_t s);
+
 // Message returned by tslb_last_error(NULL) (calls that have no context).
 void set_global_error(const char* msg);
 
