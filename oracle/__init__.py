@@ -63,6 +63,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("ext_force", ctypes.c_double * 3),
         ("normal_eps", ctypes.c_double),
+        ("ce_neq", ctypes.c_int),
     ]
 
 
@@ -95,6 +96,7 @@ def lib():
             l.orc_feq3.argtypes = [ctypes.c_double, _D, _D]
             l.orc_interface.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D]
             l.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
+            l.orc_ce_neq.argtypes = [_D, ctypes.c_double, _D]
             l.orc_inlet_state.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int64, _D, _D]
             _lib = l
@@ -115,7 +117,7 @@ def _f64(a, n=None) -> np.ndarray:
 def make_params(nx, ny, nz, omega, sigma=0.0, gamma=0.0, faces=(0, 0, 0, 0, 0, 0),
                 inlet_u=(0.0, 0.0, 0.0), inlet_diameter=0.0, inlet_cx=0.0, inlet_cy=0.0,
                 inlet_width=3.0, noise_amp=0.0, seed=0, ext_force=(0.0, 0.0, 0.0),
-                normal_eps=1e-2) -> Params:
+                normal_eps=1e-2, ce_neq=False) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.omega, p.sigma, p.gamma = float(omega), float(sigma), float(gamma)
@@ -130,6 +132,7 @@ def make_params(nx, ny, nz, omega, sigma=0.0, gamma=0.0, faces=(0, 0, 0, 0, 0, 0
     p.noise_amp = float(noise_amp)
     p.seed = int(seed)
     p.normal_eps = float(normal_eps)
+    p.ce_neq = 1 if ce_neq else 0
     return p
 
 
@@ -215,6 +218,14 @@ def interface(phi27, sigma, eps=1e-2):
     lib().orc_interface(_dp(_f64(phi27, 27)), float(sigma), float(eps), _dp(g), _dp(h), _dp(n),
                         ctypes.byref(k), _dp(F))
     return g, h, n, k.value, F
+
+
+def ce_neq(j27, omega) -> np.ndarray:
+    """Chapman-Enskog a2_neq (xx, yy, zz, xy, xz, yz) from the momentum j of the
+    27 neighbours (27 x 3, oracle direction order)."""
+    out = np.empty(6)
+    lib().orc_ce_neq(_dp(_f64(j27, 81)), float(omega), _dp(out))
+    return out
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

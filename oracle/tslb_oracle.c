@@ -179,7 +179,7 @@ void orc_feq3(double rho, const double* u, double* f27) {
  * a3_abg = u_a a2_bg + u_b a2_ag + u_g a2_ab (Eq. noneqts),
  * f^neq_i = w_i [c.a1/cs2 + H2:a2/(2 cs^4) + H3:a3/(6 cs^6)] (Eq. neq_final),
  * S_i = w_i [c.F/cs2 + H2:(uF + Fu)/(2 cs^4)]. */
-static void post_f(const node_t* nd, const double* F, double omega, double* f) {
+static void post_f(const node_t* nd, const double* F, double omega, const double (*a2_ce)[3], double* f) {
     const double rho = nd->rho;
     double u[3], a1[3], a2[3][3], a3[3][3][3], uf[3][3];
     for (int a = 0; a < 3; ++a) {
@@ -189,7 +189,7 @@ static void post_f(const node_t* nd, const double* F, double omega, double* f) {
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             double pi_ab = rho * CS2 * (a == b) + rho * nd->u[a] * nd->u[b] + nd->P[a][b];
-            a2[a][b] = pi_ab - (rho * CS2 * (a == b) + rho * u[a] * u[b]);
+            a2[a][b] = a2_ce ? a2_ce[a][b] : pi_ab - (rho * CS2 * (a == b) + rho * u[a] * u[b]);
             uf[a][b] = u[a] * F[b] + F[a] * u[b];
         }
     for (int a = 0; a < 3; ++a)
@@ -229,7 +229,20 @@ void orc_post_populations(double rho, const double* u_raw, const double* pi,
     nd.P[1][2] = nd.P[2][1] = pi[5];
     nd.phi = 0;
     nd.inlet = 0;
-    post_f(&nd, force, 1.0 * omega, f27);
+    post_f(&nd, force, 1.0 * omega, NULL, f27);
+}
+
+/* Chapman-Enskog non-equilibrium second moment from the momentum of the 27
+ * neighbours, j(x + c_i) (i in oracle order): grad j by the isotropic stencil
+ * (1/cs2) sum_i w_i c_i j(x + c_i), a2 = -(cs2/omega)(d_a j_b + d_b j_a). */
+void orc_ce_neq(const double* j27 /* 27 x 3 */, double omega, double* a2_6) {
+    tables();
+    double d[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  /* d[a][b] = d_a j_b */
+    for (int i = 0; i < Q; ++i)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) d[a][b] += W[i] * C[i][a] * j27[3 * i + b] / CS2;
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) a2_6[k] = -(CS2 / omega) * (d[ia[k]][ib[k]] + d[ib[k]][ia[k]]);
 }
 
 /* D3Q7 post-collision populations, tau = 1 (Eq. intcapturing, antidiff). */
@@ -355,7 +368,19 @@ static void node_post(const fields_t* fs, int gx, int gy, int gz, double* f, dou
         orc_interface(phi27, p->sigma, p->normal_eps, NULL, NULL, nrm, NULL, F);
         for (int a = 0; a < 3; ++a) F[a] += p->ext_force[a];
     }
-    post_f(&nd, F, p->omega, f);
+    double a2[3][3];
+    if (p->ce_neq) {
+        double j27[3 * Q], a2_6[6];
+        for (int i = 0; i < Q; ++i) {
+            node_t nb;
+            fetch_node(fs, gx + C[i][0], gy + C[i][1], gz + C[i][2], &nb);
+            for (int a = 0; a < 3; ++a) j27[3 * i + a] = nb.rho * nb.u[a];
+        }
+        orc_ce_neq(j27, p->omega, a2_6);
+        const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+        for (int k = 0; k < 6; ++k) a2[ia[k]][ib[k]] = a2[ib[k]][ia[k]] = a2_6[k];
+    }
+    post_f(&nd, F, p->omega, p->ce_neq ? (const double(*)[3])a2 : NULL, f);
     double u[3];
     for (int a = 0; a < 3; ++a) u[a] = nd.u[a] + F[a] / (2.0 * nd.rho);
     post_g(nd.phi, u, nrm, p->gamma, g);

@@ -45,6 +45,8 @@ typedef struct {
     uint64_t seed;           /* Philox key of the inlet noise */
     double ext_force[3];     /* test hook: uniform body force added to the interface force */
     double normal_eps;       /* regularisation of the interface normal, n = grad phi / sqrt(|grad phi|^2 + eps^2) */
+    int ce_neq;              /* 1: a2_neq from the Chapman-Enskog strain rate of the neighbours'
+                                momentum, -(cs2/omega)(d_a j_b + d_b j_a), instead of Pi - Pi^eq */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -83,6 +85,7 @@ void orc_feq3(double rho, const double* u, double* f27);
 void orc_interface(const double* phi27 /* phi(x + c_i), i in oracle order */,
                    double sigma, double eps, double* grad3, double* hess6, double* normal3,
                    double* kappa, double* force3);
+void orc_ce_neq(const double* j27, double omega, double* a2_6);
 void orc_philox4x32_10(const uint32_t* ctr4, const uint32_t* key2, uint32_t* out4);
 void orc_inlet_state(const orc_params* p, int x, int y, int64_t t, double* u3, double* phi);
 
