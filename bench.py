@@ -35,7 +35,7 @@ UNIT = "GLUPS"
 FIELDS = 11  # stored values per node: rho - 1, u (3), P (6), phi
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_jet192_fp32.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2403_15773_gb300", "csrc", f)
-                  for f in ("tslb_step.cu", "tslb_internal.h")]
+                  for f in ("tslb_step.cu", "tslb_device.cuh", "tslb_internal.h")]
 
 
 def kernel_source_sha() -> str:
@@ -145,13 +145,14 @@ def describe(w) -> str:
 
 # ------------------------------------------------------------- CPU oracle leg
 
-def oracle_params_of(w):
+def oracle_params_of(w, ce_neq=False):
     import oracle
     faces = {"periodic": oracle.PERIODIC, "inlet": oracle.INLET, "outflow": oracle.OUTFLOW,
              "free_slip": oracle.FREE_SLIP}
     return oracle.make_params(w.nx, w.ny, w.nz, w.omega, w.sigma, 1.0 / w.width,
                               [faces[f] for f in w.faces], w.inlet_u, w.inlet_diameter, w.inlet_cx,
-                              w.inlet_cy, w.width, w.noise_amp, w.seed, normal_eps=w.normal_eps)
+                              w.inlet_cy, w.width, w.noise_amp, w.seed, normal_eps=w.normal_eps,
+                              ce_neq=ce_neq)
 
 
 def oracle_sample_workload(w, dims=(64, 64, 32)):
@@ -202,15 +203,36 @@ def whole_job_rate(nodes_per_rank: int, world: int, steps: int, ms_max: float) -
 
 # ------------------------------------------------------------------ GPU leg
 
+def variant_form(name: str):
+    """(storage, scheme, closure) of a measured form: fp32 / fp16 / bf16
+    storage, two_sweep (the paper's population design), ce[_fp16|_bf16] (the
+    Chapman-Enskog closure, 5 stored fields)."""
+    if name == "two_sweep":
+        return "fp32", "two_sweep", "projection"
+    if name.startswith("ce"):
+        return (name[3:] or "fp32"), "fused", "chapman_enskog"
+    return name, "fused", "projection"
+
+
+def stored_bytes_per_node(name: str) -> int:
+    """Algorithmic HBM bytes per node and step of a form: every stored value
+    read once and written once (two_sweep: 11 moments + 34 populations)."""
+    st, scheme, closure = variant_form(name)
+    if scheme == "two_sweep":
+        return (11 + 34) * 2 * 4
+    return (5 if closure == "chapman_enskog" else FIELDS) * 2 * (4 if st == "fp32" else 2)
+
+
 def run_gpu(args, w, storage: str, rank: int, world: int, dist):
     import torch
     import paper_2403_15773_gb300 as tslb
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream()
-    two = storage == "two_sweep"
-    sim = tslb.Simulation(w, storage="fp32" if two else storage, stream=stream,
+    st, scheme, closure = variant_form(storage)
+    two = scheme == "two_sweep"
+    sim = tslb.Simulation(w, storage=st, stream=stream,
                           block_warps=0 if two else args.block_warps, tile_z=0 if two else args.tile_z,
-                          scheme="two_sweep" if two else "fused")
+                          scheme=scheme, closure=closure)
     rho, u, phi = w.fields()
     sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
     shape = None
@@ -338,13 +360,14 @@ def run_e2e(args, w, storage: str, world: int = 1, dist=None):
 
 def variant_line(args, w, storage, res, base_glups):
     glups = w.nodes * args.steps / (res["ms"] * 1e-3) / 1e9
-    # two_sweep: 11 moments + 34 populations, each read once and written once
-    bpn = (11 + 34) * 2 * 4 if storage == "two_sweep" else FIELDS * 2 * (4 if storage == "fp32" else 2)
+    bpn = stored_bytes_per_node(storage)
+    st, scheme, closure = variant_form(storage)
     peak, _ = measured_peaks()
     ach = bpn * w.nodes / (res["ms"] * 1e-3 / args.steps) / 1e9
-    return {"storage": storage, "value": glups, "unit": UNIT, "speedup_vs_fp32": glups / base_glups,
-            "ms_per_step": res["ms"] / args.steps, "bytes_per_node": bpn, "hbm_frac": ach / peak,
-            "state_gb": (45 * 4 if storage == "two_sweep" else bpn) * w.nodes / 1e9}
+    return {"storage": st, "scheme": scheme, "closure": closure, "value": glups, "unit": UNIT,
+            "speedup_vs_fp32": glups / base_glups, "ms_per_step": res["ms"] / args.steps,
+            "bytes_per_node": bpn, "hbm_frac": ach / peak, "gpu_launches": res["launches"],
+            "tile": res["shape"], "state_gb": (45 * 4 if scheme == "two_sweep" else bpn) * w.nodes / 1e9}
 
 
 def oracle_errors(w, storages, steps=200):
@@ -356,20 +379,25 @@ def oracle_errors(w, storages, steps=200):
     from paper_2403_15773_gb300 import inputs
     c = inputs.crop_jet(w, 48, 48, 48, diameter=8) if w.kind == "jet" else w
     rho, u, phi = c.fields()
-    ref = oracle.OracleSim(oracle_params_of(c))
-    ref.set_state(rho, u, phi)
-    ref.step(steps)
-    r = ref.moments()
+    refs = {}
     out = {}
-    for st in storages:
-        sim = (tslb.Simulation(c, scheme="two_sweep") if st == "two_sweep" else tslb.Simulation(c, storage=st))
+    for name in storages:
+        st, scheme, closure = variant_form(name)
+        ce = closure == "chapman_enskog"
+        if ce not in refs:  # each closure against the oracle run with it
+            ref = oracle.OracleSim(oracle_params_of(c, ce_neq=ce))
+            ref.set_state(rho, u, phi)
+            ref.step(steps)
+            refs[ce] = ref.moments()
+        r = refs[ce]
+        sim = tslb.Simulation(c, storage=st, scheme=scheme, closure=closure)
         sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
         sim.step(steps)
         g = sim.fields_numpy()
         sim.close()
-        out[st] = {"rho": float(np.max(np.abs(g[0] - r[0])) / np.max(np.abs(r[0]))),
-                   "u": float(np.max(np.abs(g[1] - r[1])) / max(np.max(np.abs(r[1])), 0.05)),
-                   "phi": float(np.max(np.abs(g[3] - r[3])))}
+        out[name] = {"rho": float(np.max(np.abs(g[0] - r[0])) / np.max(np.abs(r[0]))),
+                     "u": float(np.max(np.abs(g[1] - r[1])) / max(np.max(np.abs(r[1])), 0.05)),
+                     "phi": float(np.max(np.abs(g[3] - r[3])))}
     case = f"{c.nx}x{c.ny}x{c.nz} crop of the workload, {steps} steps, max error (rho / max rho, u / max(max u, 0.05), phi)"
     return out, case
 
@@ -382,9 +410,10 @@ def main():
     ap.add_argument("--impl", default="tslb", choices=["tslb", "reference"])
     ap.add_argument("--workload", default="jet192")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
-    ap.add_argument("--variants", default="fp16,bf16,two_sweep",
-                    help="extra forms measured on the same workload: fp16, bf16 storage and "
-                         "two_sweep (the paper's population design) ('' for none)")
+    ap.add_argument("--variants", default="fp16,bf16,two_sweep,ce,ce_fp16",
+                    help="extra forms measured on the same workload: fp16, bf16 storage, "
+                         "two_sweep (the paper's population design), ce, ce_fp16, ce_bf16 (the "
+                         "Chapman-Enskog closure, 5 stored fields) ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true")
@@ -430,6 +459,11 @@ def main():
         errs, err_case = oracle_errors(w, [args.storage] + vlist)
         for v in vlist:
             variants[v]["oracle_err"] = errs[v]
+    for v in variants:
+        if v.startswith("ce"):
+            variants[v]["note"] = ("Chapman-Enskog closure of a2_neq (Sec. 2.1): 5 stored fields, P "
+                                   "neither stored nor read; a different closure, so oracle_err is "
+                                   "against the oracle run with the same closure")
     if "two_sweep" in variants:
         variants["two_sweep"]["note"] = ("the paper's design on this GPU: collide+push into 34 population "
                                          "arrays, then their moments; fused speedup over it = "

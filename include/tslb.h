@@ -58,7 +58,8 @@ typedef enum {
 
 typedef enum { TSLB_LATTICE_D3Q27_D3Q7 = 0 } tslb_lattice;
 
-/* Storage of the 11 per-node fields in HBM.  All arithmetic is FP32. */
+/* Storage of the per-node fields in HBM (11, or 5 under the Chapman-Enskog
+ * closure).  All arithmetic is FP32. */
 typedef enum { TSLB_FP32 = 0, TSLB_FP16 = 1, TSLB_BF16 = 2 } tslb_storage;
 
 /* Face rules.  INLET is allowed on the -z face only. */
@@ -73,6 +74,17 @@ typedef enum {
 typedef struct {
     int32_t nx, ny, nz; /* nodes per axis; >= 1 on periodic axes, >= 2 otherwise */
 } tslb_grid;
+
+/* Closure of the non-equilibrium second moment a2_neq of the collision
+ * (Sec. 2.1).
+ * PROJECTION: a2_neq = Pi - Pi^eq of the stored moments; the state holds
+ *   rho - 1, u, P, phi (11 fields).
+ * CHAPMAN_ENSKOG: a2_neq = -(cs2/omega)(d_a j_b + d_b j_a), the strain rate of
+ *   j = rho u by the isotropic D3Q27 gradient stencil, evaluated at every node
+ *   and ghost over the ghost-resolved momentum field; the state holds rho - 1,
+ *   u, phi (5 fields) and P does not exist (tslb_get_moments refuses pi,
+ *   tslb_set_state ignores it).  Single grids, scheme 0, block_warps 8 or 12. */
+typedef enum { TSLB_CLOSURE_PROJECTION = 0, TSLB_CLOSURE_CHAPMAN_ENSKOG = 1 } tslb_closure;
 
 /* Boundary specification.  The inlet imposes on the -z face a smoothed top
  * hat of diameter inlet_diameter centred at (inlet_cx, inlet_cy):
@@ -110,6 +122,8 @@ typedef struct {
     int32_t average;        /* 1: every step also adds the new phi and u_z of each node to FP64
                                time sums (the time-averaged fields of Sec. 3: centre-line and
                                radial profiles of <phi> and <u_z>); 0 = off (default) */
+    int32_t closure;        /* tslb_closure of the non-equilibrium second moment; default
+                               TSLB_CLOSURE_PROJECTION */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
                                (blocking, so ordered with the legacy default stream) */
 } tslb_options;
@@ -136,7 +150,8 @@ TSLB_API tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_latti
                       void* workspace, size_t workspace_bytes);
 
 /* Sets the state from rho[N], u[3N] and phi[N]; pi[6N] sets P (NULL = 0, i.e.
- * the populations start at the third-order equilibrium).  Step index := 0. */
+ * the populations start at the third-order equilibrium; ignored under the
+ * Chapman-Enskog closure).  Step index := 0. */
 TSLB_API tslb_status tslb_set_state(tslb_ctx* ctx, const float* rho, const float* u, const float* pi,
                            const float* phi, int on_device);
 
@@ -147,7 +162,8 @@ TSLB_API tslb_status tslb_set_state(tslb_ctx* ctx, const float* rho, const float
  * rho and phi of the new state. */
 TSLB_API tslb_status tslb_step(tslb_ctx* ctx, int64_t n);
 
-/* Copies the current moments out (rho[N], u[3N], pi[6N]; any may be NULL). */
+/* Copies the current moments out (rho[N], u[3N], pi[6N]; any may be NULL;
+ * pi must be NULL under the Chapman-Enskog closure, else TSLB_ERR_INVALID_ARG). */
 TSLB_API tslb_status tslb_get_moments(tslb_ctx* ctx, float* rho, float* u, float* pi, int on_device);
 
 /* Copies the current phase field out (phi[N]). */
@@ -161,9 +177,10 @@ TSLB_API tslb_status tslb_sums(tslb_ctx* ctx, double* mass, double* phi_total);
 /* Number of steps taken since tslb_set_state / tslb_put_state. */
 TSLB_API tslb_status tslb_get_time(const tslb_ctx* ctx, int64_t* t);
 
-/* Checkpoint: the raw stored fields (11 N values of the storage type) plus
- * the step index, tslb_state_bytes() bytes in total.  put_state restores a
- * buffer written by get_state of a context with the same grid and storage. */
+/* Checkpoint: the raw stored fields (11 N values of the storage type, 5 N
+ * under the Chapman-Enskog closure) plus the step index, tslb_state_bytes()
+ * bytes in total.  put_state restores a buffer written by get_state of a
+ * context with the same grid, storage and closure. */
 TSLB_API size_t tslb_state_bytes(const tslb_ctx* ctx);
 TSLB_API tslb_status tslb_get_state(tslb_ctx* ctx, void* dst, int on_device);
 TSLB_API tslb_status tslb_put_state(tslb_ctx* ctx, const void* src, int on_device);

@@ -36,6 +36,7 @@ TSLB_OK, TSLB_ERR_INVALID_ARG, TSLB_ERR_OOM, TSLB_ERR_CUDA, TSLB_ERR_UNSTABLE, T
     TSLB_ERR_STATE = range(7)
 TSLB_LATTICE_D3Q27_D3Q7 = 0
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+CLOSURES = {"projection": 0, "chapman_enskog": 1}
 FACES = {"periodic": 0, "inlet": 1, "outflow": 2, "free_slip": 3}
 
 SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_set_state", "tslb_step",
@@ -62,7 +63,8 @@ class Options(ctypes.Structure):
                 ("normal_eps", ctypes.c_float), ("field_scale", ctypes.c_float * 4),
                 ("check_every", ctypes.c_int32), ("tile_z", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("block_warps", ctypes.c_int32),
-                ("scheme", ctypes.c_int32), ("average", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("scheme", ctypes.c_int32), ("average", ctypes.c_int32), ("closure", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class TslbError(RuntimeError):
@@ -320,7 +322,7 @@ class Simulation:
 
     def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
                  graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0,
-                 average: bool = False, scheme: str = "fused"):
+                 average: bool = False, scheme: str = "fused", closure: str = "projection"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Simulation needs a CUDA device")
@@ -338,6 +340,8 @@ class Simulation:
         o.block_warps = int(block_warps)
         o.average = 1 if average else 0
         o.scheme = {"fused": 0, "two_sweep": 1}[scheme]
+        o.closure = CLOSURES[closure]
+        self.closure = closure
         if field_scale is not None:
             for g in range(4):
                 o.field_scale[g] = float(field_scale[g])
@@ -383,11 +387,15 @@ class Simulation:
         tslb_step(self.ctx, n)
 
     def moments(self):
-        """(rho[N], u[3, N], pi[6, N]) as float32 CUDA tensors."""
+        """(rho[N], u[3, N], pi[6, N]) as float32 CUDA tensors; pi is None
+        under the Chapman-Enskog closure (P is not part of its state)."""
         import torch
         N = self.N
         rho = torch.empty(N, dtype=torch.float32, device="cuda")
         u = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+        if self.closure == "chapman_enskog":
+            tslb_get_moments(self.ctx, rho.data_ptr(), u.data_ptr(), 0, 1)
+            return rho, u.view(3, N), None
         pi = torch.empty(6 * N, dtype=torch.float32, device="cuda")
         tslb_get_moments(self.ctx, rho.data_ptr(), u.data_ptr(), pi.data_ptr(), 1)
         return rho, u.view(3, N), pi.view(6, N)
@@ -410,7 +418,7 @@ class Simulation:
         rho, u, pi = self.moments()
         ph = self.phi()
         s = (self.workload.nz, self.workload.ny, self.workload.nx)
-        f = lambda t, lead: t.double().cpu().numpy().reshape(lead + s)
+        f = lambda t, lead: None if t is None else t.double().cpu().numpy().reshape(lead + s)
         return f(rho, ()), f(u, (3,)), f(pi, (6,)), f(ph, ())
 
     def sums(self):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libtslb.so")
-SOURCES = ["tslb_step.cu", "tslb_api.cu", "tslb_noalloc.cu", "tslb_twosweep.cu"]
+SOURCES = ["tslb_step.cu", "tslb_step_ce.cu", "tslb_api.cu", "tslb_noalloc.cu", "tslb_twosweep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE, "-I" + CSRC]

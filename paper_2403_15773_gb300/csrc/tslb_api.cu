@@ -161,6 +161,14 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
         why = "block_warps must be 0, 8, 12 or 16";
         return false;
     }
+    if (opt->closure != TSLB_CLOSURE_PROJECTION && opt->closure != TSLB_CLOSURE_CHAPMAN_ENSKOG) {
+        why = "unknown closure";
+        return false;
+    }
+    if (opt->closure == TSLB_CLOSURE_CHAPMAN_ENSKOG && opt->block_warps == 16) {
+        why = "the Chapman-Enskog closure runs blocks of 8 or 12 warps";
+        return false;
+    }
     if (b.face[4] == TSLB_BC_INLET && !(b.inlet_diameter >= 0.f)) {
         why = "inlet_diameter must be >= 0";
         return false;
@@ -171,6 +179,7 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     p.nz = grid->nz;
     for (int k = 0; k < 6; ++k) p.face[k] = b.face[k];
     p.block_warps = opt->block_warps > 0 ? opt->block_warps : 8;
+    p.closure = opt->closure;
     p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz)
                                : auto_tile_z(grid, p.block_warps, 152);
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
@@ -258,7 +267,7 @@ Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, b
     int tiles = 0, conv = 0;
     for (const StepParams& p : ps) {
         L.state.push_back(off);
-        off += 2 * align256(tslb::NFIELDS * (size_t)p.fstride * elem);
+        off += 2 * align256(tslb::stored_fields(p.closure) * (size_t)p.fstride * elem);
         L.avg.push_back(off);
         if (average) off += align256(2 * (size_t)p.fstride * sizeof(double));
         maxf = std::max(maxf, p.fstride);
@@ -345,6 +354,11 @@ cudaError_t launch_one(tslb_ctx* c, int q) {
         Instance& I = c->inst[0];
         return tslb::launch_twosweep_step(I.p, static_cast<float*>(I.buf[0]), c->pops, c->tdev + q,
                                           c->tdev + (q ^ 1), c->partials, c->stream);
+    }
+    if (!c->batch && c->inst[0].p.closure == tslb::CL_CHAPMAN_ENSKOG) {
+        Instance& I = c->inst[0];
+        return tslb::launch_step_ce(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
+                                    c->partials, c->stream);
     }
     if (!c->batch) {
         Instance& I = c->inst[0];
@@ -459,6 +473,10 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
         g_init_err = "the two-sweep scheme runs single grids in FP32 without averages";
         return TSLB_ERR_INVALID_ARG;
     }
+    if (o.closure == TSLB_CLOSURE_CHAPMAN_ENSKOG && (batch || o.scheme != 0)) {
+        g_init_err = "the Chapman-Enskog closure runs single grids with the fused scheme";
+        return TSLB_ERR_INVALID_ARG;
+    }
     std::vector<StepParams> ps(count);
     for (int i = 0; i < count; ++i) {
         std::string why;
@@ -492,6 +510,7 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
         return fail(TSLB_ERR_CUDA);
     }
     e = tslb::prepare_kernels(c->storage);
+    if (e == cudaSuccess && o.closure == TSLB_CLOSURE_CHAPMAN_ENSKOG) e = tslb::prepare_kernels_ce(c->storage);
     if (e == cudaSuccess && batch) e = tslb::prepare_batch_kernels();
     if (e != cudaSuccess) {
         c->err = std::string("kernel set-up: ") + cudaGetErrorString(e);
@@ -539,7 +558,7 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
         I.p = ps[i];
         I.N = (long long)grids[i].nx * grids[i].ny * grids[i].nz;
         I.buf[0] = base + L.state[i];
-        I.buf[1] = base + L.state[i] + align256(tslb::NFIELDS * (size_t)ps[i].fstride * c->elem);
+        I.buf[1] = base + L.state[i] + align256(tslb::stored_fields(ps[i].closure) * (size_t)ps[i].fstride * c->elem);
         if (c->average) {
             I.avg = reinterpret_cast<double*>(base + L.avg[i]);
             I.p.avg = I.avg;
@@ -583,7 +602,9 @@ tslb_status set_state_of(tslb_ctx* c, int i, const float* rho, const float* u, c
     if ((s = put_field(c, I, rho, tslb::F_DRHO, on_device)) != TSLB_OK) return s;
     for (int a = 0; a < 3; ++a)
         if ((s = put_field(c, I, u + a * N, tslb::F_UX + a, on_device)) != TSLB_OK) return s;
-    if (pi) {
+    if (I.p.closure == tslb::CL_CHAPMAN_ENSKOG) {
+        // P is not part of the state
+    } else if (pi) {
         for (int k = 0; k < 6; ++k)
             if ((s = put_field(c, I, pi + k * N, tslb::F_PXX + k, on_device)) != TSLB_OK) return s;
     } else {
@@ -613,6 +634,8 @@ tslb_status get_moments_of(tslb_ctx* c, int i, float* rho, float* u, float* pi, 
     if (!I.set) return bad(c, "no state", TSLB_ERR_STATE);
     if (on_device && ((rho && !is_device_ptr(rho)) || (u && !is_device_ptr(u)) || (pi && !is_device_ptr(pi))))
         return bad(c, "on_device pointers must be device memory");
+    if (pi && I.p.closure == tslb::CL_CHAPMAN_ENSKOG)
+        return bad(c, "the Chapman-Enskog closure stores no P: pi must be NULL");
     CK(cudaSetDevice(c->device), "set device");
     const long long N = I.N;
     tslb_status s;
@@ -882,7 +905,7 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
 
 size_t tslb_state_bytes(const tslb_ctx* c) {
     if (!c) return 0;
-    return (size_t)tslb::NFIELDS * (size_t)c->inst[0].N * c->elem + sizeof(int64_t);
+    return (size_t)tslb::stored_fields(c->inst[0].p.closure) * (size_t)c->inst[0].N * c->elem + sizeof(int64_t);
 }
 
 tslb_status tslb_get_state(tslb_ctx* c, void* dst, int on_device) {
@@ -893,19 +916,20 @@ tslb_status tslb_get_state(tslb_ctx* c, void* dst, int on_device) {
     if (on_device && !is_device_ptr(dst)) return bad(c, "on_device pointers must be device memory");
     CK(cudaSetDevice(c->device), "set device");
     const size_t fb = (size_t)I.N * c->elem;
+    const int nf = tslb::stored_fields(I.p.closure);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    for (int f = 0; f < tslb::NFIELDS; ++f)
+    for (int f = 0; f < nf; ++f)
         CK(cudaMemcpyAsync(static_cast<char*>(dst) + f * fb,
                            static_cast<const char*>(I.buf[c->cur]) + (size_t)f * I.p.fstride * c->elem, fb, kind,
                            c->stream),
            "state copy");
     int64_t t = c->t;
     if (on_device)
-        CK(cudaMemcpyAsync(static_cast<char*>(dst) + tslb::NFIELDS * fb, &t, sizeof(t), cudaMemcpyHostToDevice,
+        CK(cudaMemcpyAsync(static_cast<char*>(dst) + nf * fb, &t, sizeof(t), cudaMemcpyHostToDevice,
                            c->stream),
            "step copy");
     CK(cudaStreamSynchronize(c->stream), "get_state synchronise");
-    if (!on_device) std::memcpy(static_cast<char*>(dst) + tslb::NFIELDS * fb, &t, sizeof(t));
+    if (!on_device) std::memcpy(static_cast<char*>(dst) + nf * fb, &t, sizeof(t));
     return TSLB_OK;
 }
 
@@ -916,19 +940,20 @@ tslb_status tslb_put_state(tslb_ctx* c, const void* src, int on_device) {
     CK(cudaSetDevice(c->device), "set device");
     Instance& I = c->inst[0];
     const size_t fb = (size_t)I.N * c->elem;
+    const int nf = tslb::stored_fields(I.p.closure);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     c->cur = 0;
-    for (int f = 0; f < tslb::NFIELDS; ++f)
+    for (int f = 0; f < nf; ++f)
         CK(cudaMemcpyAsync(static_cast<char*>(I.buf[0]) + (size_t)f * I.p.fstride * c->elem,
                            static_cast<const char*>(src) + f * fb, fb, kind, c->stream),
            "state copy");
     int64_t t = 0;
     if (on_device)
-        CK(cudaMemcpyAsync(&t, static_cast<const char*>(src) + tslb::NFIELDS * fb, sizeof(t), cudaMemcpyDeviceToHost,
+        CK(cudaMemcpyAsync(&t, static_cast<const char*>(src) + nf * fb, sizeof(t), cudaMemcpyDeviceToHost,
                            c->stream),
            "step copy");
     else
-        std::memcpy(&t, static_cast<const char*>(src) + tslb::NFIELDS * fb, sizeof(t));
+        std::memcpy(&t, static_cast<const char*>(src) + nf * fb, sizeof(t));
     CK(cudaStreamSynchronize(c->stream), "put_state synchronise");
     if (t < 0) return bad(c, "negative step index in checkpoint");
     long long tt[2] = {(long long)t, (long long)t};

@@ -16,12 +16,24 @@ enum {
     F_DRHO = 0, F_UX, F_UY, F_UZ, F_PXX, F_PYY, F_PZZ, F_PXY, F_PXZ, F_PYZ, F_PHI, NFIELDS
 };
 
+// Closure of the non-equilibrium second moment: the projection Pi - Pi^eq of
+// the stored P (all 11 fields stored), or the Chapman-Enskog estimate from the
+// strain rate of the momentum field (P not stored: rho - 1, u, phi in slots
+// 0..4).
+enum { CL_PROJECTION = 0, CL_CHAPMAN_ENSKOG = 1 };
+inline __host__ __device__ int stored_fields(int closure) { return closure == CL_CHAPMAN_ENSKOG ? 5 : NFIELDS; }
+// Buffer slot of field f (f must be stored under the closure).
+inline __host__ __device__ int field_slot(int closure, int f) {
+    return closure == CL_CHAPMAN_ENSKOG && f == F_PHI ? 4 : f;
+}
+
 // Everything the step kernel needs, passed by value (__grid_constant__).
 struct StepParams {
     int nx, ny, nz;
     int face[6];
     int tile_z;
     int block_warps;         // warps per block of the step kernel (8, 12 or 16)
+    int closure;             // CL_PROJECTION or CL_CHAPMAN_ENSKOG
     long long fstride;       // elements between consecutive fields of a buffer
     float omega, sigma, gamma, normal_eps2;
     float inlet_u[3], inlet_umag, inlet_half_d, inlet_cx, inlet_cy, inlet_two_over_w, noise_amp;
@@ -54,6 +66,12 @@ cudaError_t launch_step(const StepParams& p, int storage, const void* in, void* 
 
 // Kernel attributes (dynamic shared memory) of the step kernel; once per device.
 cudaError_t prepare_kernels(int storage);
+
+// Step kernel of the Chapman-Enskog closure (tslb_step_ce.cu; FP32 or 16-bit
+// storage, blocks of 8 or 12 warps), same contract as launch_step.
+cudaError_t launch_step_ce(const StepParams& p, int storage, const void* in, void* out,
+                           const long long* t_in, long long* t_out, double* partials, cudaStream_t s);
+cudaError_t prepare_kernels_ce(int storage);
 
 // One caller field (float, device) -> one stored field (rho - 1 for F_DRHO).
 cudaError_t launch_put_field(const StepParams& p, int storage, const float* src, int field,

@@ -34,178 +34,10 @@
 //
 // All arithmetic is FP32 and works with deviations from the rest state
 // (rho - 1, Pi - cs2 I) so that no O(1) terms cancel.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include "tslb_internal.h"
+#include "tslb_device.cuh"
 
 namespace tslb {
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int TX = 30;        // interior columns of a tile; a warp stages TX + 2
-constexpr int PHX = TX + 4;   // phase-field columns of a tile (halo 2)
-
-// ------------------------------------------------------------------ helpers
-
-// Source coordinate of grid coordinate g on an axis of n nodes whose lower /
-// upper faces follow rule lo / hi.  sign = -1 for a mirror image, inlet = 1
-// for the inlet ghost.  Coordinates farther out than any stencil reaches are
-// clamped into the grid (their values are never used).
-__device__ __forceinline__ int resolve_axis(int g, int n, int lo, int hi, float& sign, int& inlet) {
-    sign = 1.f;
-    if (g >= 0 && g < n) return g;
-    const int kind = g < 0 ? lo : hi;
-    int s;
-    if (kind == BC_PERIODIC) {
-        s = g % n;
-        if (s < 0) s += n;
-    } else if (kind == BC_FREE_SLIP) {
-        sign = -1.f;
-        s = g < 0 ? -1 - g : 2 * n - 1 - g;
-    } else {
-        if (kind == BC_INLET) inlet = 1;
-        s = g < 0 ? 0 : n - 1;
-    }
-    return min(max(s, 0), n - 1);
-}
-
-// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11).
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0;
-        c[1] = lo1;
-        c[2] = n2;
-        c[3] = lo0;
-    }
-}
-
-// Imposed phase field of the inlet at lateral node (x, y): smoothed top hat.
-__device__ __forceinline__ float inlet_phi(const StepParams& P, int x, int y) {
-    const float dx = (float)x - P.inlet_cx, dy = (float)y - P.inlet_cy;
-    const float r = sqrtf(dx * dx + dy * dy);
-    return -tanhf((r - P.inlet_half_d) * P.inlet_two_over_w);
-}
-
-// Imposed inlet velocity at (x, y) and step t: s (U + xi), s = (1 + phi_B)/2,
-// xi_c = a |U| (2 r_c - 1), r_c from Philox on counter (x + nx y, t_lo, t_hi, 0).
-__device__ void inlet_velocity(const StepParams& P, int x, int y, long long t, float u[3]) {
-    const float s = 0.5f * (1.f + inlet_phi(P, x, y));
-    uint32_t c[4] = {(uint32_t)(x + P.nx * y), (uint32_t)((unsigned long long)t & 0xffffffffu),
-                     (uint32_t)((unsigned long long)t >> 32), 0u};
-    philox4x32_10(c, P.seed_lo, P.seed_hi);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float rc = (float)(c[k] >> 8) * (1.f / 16777216.f);
-        const float xi = P.noise_amp * P.inlet_umag * (2.f * rc - 1.f);
-        u[k] = s * (P.inlet_u[k] + xi);
-    }
-}
-
-__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// Stored <-> FP32 conversion of one field value.
-template <typename S>
-struct Io;
-template <>
-struct Io<float> {
-    static constexpr bool kAsync = true;
-    static __device__ __forceinline__ float from_raw(unsigned short, float) { return 0.f; }
-    static __device__ __forceinline__ float ld(const float* p, float) { return __ldg(p); }
-    static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
-    static __device__ __forceinline__ float round_trip(float v, float, float) { return v; }
-};
-template <>
-struct Io<__half> {
-    static constexpr bool kAsync = false;
-    static __device__ __forceinline__ float from_raw(unsigned short r, float inv) {
-        return __half2float(__ushort_as_half(r)) * inv;
-    }
-    static __device__ __forceinline__ float ld(const __half* p, float inv) { return __half2float(__ldg(p)) * inv; }
-    static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
-    static __device__ __forceinline__ float round_trip(float v, float s, float inv) {
-        return __half2float(__float2half_rn(v * s)) * inv;
-    }
-};
-template <>
-struct Io<__nv_bfloat16> {
-    static constexpr bool kAsync = false;
-    static __device__ __forceinline__ float from_raw(unsigned short r, float inv) {
-        return __bfloat162float(__ushort_as_bfloat16(r)) * inv;
-    }
-    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, float inv) {
-        return __bfloat162float(__ldg(p)) * inv;
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v, float s) { *p = __float2bfloat16_rn(v * s); }
-    static __device__ __forceinline__ float round_trip(float v, float s, float inv) {
-        return __bfloat162float(__float2bfloat16_rn(v * s)) * inv;
-    }
-};
-
-// ------------------------------------------------------- packed FP32 helpers
-
-// Two lattice nodes per thread (rows 2w and 2w+1 of the tile) are processed
-// together with the packed FP32 instructions of sm_100+ (one instruction, two
-// lanes of arithmetic): .x is the node of row 2w, .y the node of row 2w+1.
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
-    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
-__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 operator*(float s, float2 b) { return __fmul2_rn(make_float2(s, s), b); }
-__device__ __forceinline__ float2 mad(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mad(float s, float2 b, float2 c) { return __ffma2_rn(make_float2(s, s), b, c); }
-__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
-__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
-__device__ __forceinline__ float2 shfl_up2(float2 v) {
-    return make_float2(__shfl_up_sync(FULL, v.x, 1), __shfl_up_sync(FULL, v.y, 1));
-}
-__device__ __forceinline__ float2 shfl_down2(float2 v) {
-    return make_float2(__shfl_down_sync(FULL, v.x, 1), __shfl_down_sync(FULL, v.y, 1));
-}
-
-// One axis of the streaming sweep.  (k0, k1, k2) are the Hermite coefficients
-// of the axis (k2 pre-multiplied by h2(+-1) = 2/3); the unnormalised 1D
-// populations (x 6) are
-//   p(-1) = k0 - k1 + k2,   p(0) = 4 k0 - 2 k2,   p(+1) = k0 + k1 + k2,
-// and after the shift the raw moments of the axis are
-//   M0 = q- + q0 + q+,   M1 = q+ - q-,   M2 = q+ + q-.
-struct Tri2 {
-    float2 m, z, p;
-};
-__device__ __forceinline__ Tri2 pops2(float2 k0, float2 k1, float2 k2) {
-    const float2 s = k0 + k2;
-    return {s - k1, mad(4.f, k0, -2.f * k2), s + k1};
-}
-// x sweep of two nodes: shifts along the warp (lanes = x), then x moments.
-__device__ __forceinline__ void xsweep2(float2 k0, float2 k1, float2 k2, float2& m0, float2& m1, float2& m2) {
-    const Tri2 t = pops2(k0, k1, k2);
-    const float2 qp = shfl_up2(t.p), qm = shfl_down2(t.m);
-    const float2 s = qp + qm;
-    m0 = s + t.z;
-    m1 = qp - qm;
-    m2 = s;
-}
-__device__ __forceinline__ float2 s0v(float2 a, float2 b, float2 c) { return mad(4.f, b, a + c); }
-__device__ __forceinline__ float2 l2v(float2 a, float2 b, float2 c) { return mad(-2.f, b, a + c); }
 
 // ----------------------------------------------------- step kernel (pairs)
 
@@ -537,55 +369,10 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
                 uz = make_float2(ua[2], ub[2]);
             }
 
-            // grad phi and Hessian: z combos from shared memory (rows 2w-1 .. 2w+2
-            // of the tile), then y combos for the row pair, then x combos
-            const float* zb = zc + ((i + 8) & 1) * 3 * NPH;
-            float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                float zS[4], zD[4], zL[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int e = (lane + 1 + dx) + PHX * (2 * w + r);
-                    const float c0 = zb[e], c1 = zb[NPH + e], c2 = zb[2 * NPH + e];
-                    zS[r] = fmaf(4.f, c0, c1);
-                    zD[r] = c2;
-                    zL[r] = fmaf(-2.f, c0, c1);
-                }
-                const float2 sm = make_float2(zS[0], zS[1]), s0 = make_float2(zS[1], zS[2]),
-                             sp = make_float2(zS[2], zS[3]);
-                const float2 dm = make_float2(zD[0], zD[1]), d0 = make_float2(zD[1], zD[2]),
-                             dp = make_float2(zD[2], zD[3]);
-                const float2 lm = make_float2(zL[0], zL[1]), l0 = make_float2(zL[1], zL[2]),
-                             lp = make_float2(zL[2], zL[3]);
-                yS[dx + 1] = s0v(sm, s0, sp);
-                yDS[dx + 1] = sp - sm;
-                yLS[dx + 1] = l2v(sm, s0, sp);
-                ySD[dx + 1] = s0v(dm, d0, dp);
-                yDD[dx + 1] = dp - dm;
-                ySL[dx + 1] = s0v(lm, l0, lp);
-            }
-            const int ec = (lane + 1) + PHX * (2 * w + 1);
-            const float2 phi = make_float2(zb[ec], zb[ec + PHX]);
-            const float2 gxp = (1.f / 72.f) * (yS[2] - yS[0]);
-            const float2 gyp = (1.f / 72.f) * s0v(yDS[0], yDS[1], yDS[2]);
-            const float2 gzp = (1.f / 72.f) * s0v(ySD[0], ySD[1], ySD[2]);
-            const float2 hxx = (1.f / 36.f) * l2v(yS[0], yS[1], yS[2]);
-            const float2 hyy = (1.f / 36.f) * s0v(yLS[0], yLS[1], yLS[2]);
-            const float2 hzz = (1.f / 36.f) * s0v(ySL[0], ySL[1], ySL[2]);
-            const float2 hxy = (1.f / 24.f) * (yDS[2] - yDS[0]);
-            const float2 hxz = (1.f / 24.f) * (ySD[2] - ySD[0]);
-            const float2 hyz = (1.f / 24.f) * s0v(yDD[0], yDD[1], yDD[2]);
-
-            // regularised normal, curvature, CSF force
-            const float2 m2 = mad(gxp, gxp, mad(gyp, gyp, mad(gzp, gzp, bc(P.normal_eps2))));
-            const float2 im = make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
-            float2 nxv = gxp * im, nyv = gyp * im, nzv = gzp * im;
-            const float2 ghg = mad(gxp, mad(gxp, hxx, 2.f * mad(gyp, hxy, gzp * hxz)),
-                                   mad(gyp, mad(gyp, hyy, 2.f * (gzp * hyz)), gzp * gzp * hzz));
-            const float2 kappa = (hxx + hyy + hzz) * im - ghg * (im * im * im);
-            const float2 fk = sig_half * kappa;
-            float2 Fx = fk * gxp, Fy = fk * gyp, Fz = fk * gzp;
+            // interface terms from the z combinations of phi at plane i
+            float2 phi, Fx, Fy, Fz, nxv, nyv, nzv;
+            interface2<NPH>(zc + ((i + 8) & 1) * 3 * NPH, lane, w, sig_half, P.normal_eps2, phi, Fx, Fy, Fz,
+                            nxv, nyv, nzv);
             if (inl_cur) {
                 Fx = Fy = Fz = bc(0.f);
                 nxv = nyv = nzv = bc(0.f);
@@ -603,48 +390,9 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
             const float2 nxy = pxy - rho * mad(ux, hfy, hfx * vy);
             const float2 nxz = pxz - rho * mad(ux, hfz, hfx * vz);
             const float2 nyz = pyz - rho * mad(uy, hfz, hfy * vz);
-            const float2 rvx = rho * vx, rvy = rho * vy, rvz = rho * vz;
-            const float2 exx = rvx * vx, eyy = rvy * vy, ezz = rvz * vz;
-            const float2 exy = rvx * vy, exz = rvx * vz, eyz = rvy * vz;
-            const float2 o1 = bc(om1), third = bc(1.f / 3.f);
-            const float2 qxx = o1 * nxx, qyy = o1 * nyy, qzz = o1 * nzz;
-            const float2 qxy = o1 * nxy, qxz = o1 * nxz, qyz = o1 * nyz;
-            const float2 Mxx = mad(third, exx, qxx), Myy = mad(third, eyy, qyy), Mzz = mad(third, ezz, qzz);
-            const float2 Mxy = mad(third, exy, qxy), Mxz = mad(third, exz, qxz), Myz = mad(third, eyz, qyz);
-            const float2 f2o = bc(2.f * fo), f1o = bc(fo);
-            const float2 A2xx = mad(f2o, vx * Fx, exx + qxx);
-            const float2 A2yy = mad(f2o, vy * Fy, eyy + qyy);
-            const float2 A2zz = mad(f2o, vz * Fz, ezz + qzz);
-            const float2 A2xy = mad(f1o, mad(vx, Fy, Fx * vy), exy + qxy);
-            const float2 A2xz = mad(f1o, mad(vx, Fz, Fx * vz), exz + qxz);
-            const float2 A2yz = mad(f1o, mad(vy, Fz, Fy * vz), eyz + qyz);
-
-            // tensor-product Hermite coefficients k_abc, index 2 pre-multiplied by
-            // 2/3, everything pre-divided by 216 (the 6^3 of the unnormalised sweeps)
-            const float2 c72 = bc(1.f / 72.f), c24 = bc(1.f / 24.f);
-            const float2 k000 = (1.f / 216.f) * drho;
-            const float2 k100 = c72 * mad(rho, ux, Fx), k010 = c72 * mad(rho, uy, Fy), k001 = c72 * mad(rho, uz, Fz);
-            const float2 k200 = c72 * A2xx, k020 = c72 * A2yy, k002 = c72 * A2zz;
-            const float2 k110 = c24 * A2xy, k101 = c24 * A2xz, k011 = c24 * A2yz;
-            const float2 tx = 2.f * vx, ty = 2.f * vy, tz = 2.f * vz;
-            const float2 k210 = c24 * mad(tx, Mxy, vy * Mxx);
-            const float2 k201 = c24 * mad(tx, Mxz, vz * Mxx);
-            const float2 k120 = c24 * mad(ty, Mxy, vx * Myy);
-            const float2 k021 = c24 * mad(ty, Myz, vz * Myy);
-            const float2 k102 = c24 * mad(tz, Mxz, vx * Mzz);
-            const float2 k012 = c24 * mad(tz, Myz, vy * Mzz);
-            const float2 k111 = (1.f / 8.f) * mad(vx, Myz, mad(vy, Mxz, vz * Mxy));
-
             float2 X[3][8];
             const float2 zero = bc(0.f);
-            xsweep2(k000, k100, k200, X[0][0], X[1][0], X[2][0]);
-            xsweep2(k010, k110, k210, X[0][1], X[1][1], X[2][1]);
-            xsweep2(k020, k120, zero, X[0][2], X[1][2], X[2][2]);
-            xsweep2(k001, k101, k201, X[0][3], X[1][3], X[2][3]);
-            xsweep2(k011, k111, zero, X[0][4], X[1][4], X[2][4]);
-            xsweep2(k021, zero, zero, X[0][5], X[1][5], X[2][5]);
-            xsweep2(k002, k102, zero, X[0][6], X[1][6], X[2][6]);
-            xsweep2(k012, zero, zero, X[0][7], X[1][7], X[2][7]);
+            collide_xsweep2(rho, drho, ux, uy, uz, vx, vy, vz, Fx, Fy, Fz, nxx, nyy, nzz, nxy, nxz, nyz, om1, fo, X);
 
             // y populations; the row pair exchanges inside the thread, the pair
             // edges go through shared memory: p(+1) of row 2w+1 to the thread
@@ -808,7 +556,7 @@ __global__ void __launch_bounds__(CONV_THREADS) put_field_kernel(const __grid_co
                                                                  const float* __restrict__ src, int field,
                                                                  S* __restrict__ st) {
     const long long N = (long long)P.nx * P.ny * P.nz;
-    S* dst = st + field * P.fstride;
+    S* dst = st + field_slot(P.closure, field) * P.fstride;
     const float sc = P.scale[field];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
@@ -826,7 +574,7 @@ __global__ void __launch_bounds__(CONV_THREADS) state_sums_kernel(const __grid_c
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         sr += Io<S>::ld(st + F_DRHO * fs + i, P.inv_scale[F_DRHO]);
-        sp += Io<S>::ld(st + F_PHI * fs + i, P.inv_scale[F_PHI]);
+        sp += Io<S>::ld(st + field_slot(P.closure, F_PHI) * fs + i, P.inv_scale[F_PHI]);
     }
     block_partials<S>(sr, sp, partials);
 }
@@ -836,7 +584,7 @@ __global__ void __launch_bounds__(CONV_THREADS) get_field_kernel(const __grid_co
                                                                  const S* __restrict__ st, int field,
                                                                  float* __restrict__ dst) {
     const long long N = (long long)P.nx * P.ny * P.nz;
-    const S* src = st + field * P.fstride;
+    const S* src = st + field_slot(P.closure, field) * P.fstride;
     const float inv = P.inv_scale[field];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {

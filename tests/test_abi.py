@@ -99,3 +99,46 @@ def test_product_code_does_not_use_the_oracle():
             if fn.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
                 src = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in src and "tslb_oracle" not in src, fn
+
+
+def test_closure_options_are_checked_before_touching_the_gpu():
+    g = tslb.Grid(8, 8, 8)
+    for kw in (dict(closure=2), dict(closure=1, block_warps=16), dict(closure=1, scheme=1)):
+        o = tslb.tslb_default_options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        with pytest.raises(tslb.TslbError) as ei:
+            tslb.tslb_init(g, 1.5, 0.0, None, o)
+        assert ei.value.status == tslb.TSLB_ERR_INVALID_ARG
+
+
+def test_chapman_enskog_state_is_five_fields():
+    g = tslb.Grid(32, 32, 32)
+    N = 32 ** 3
+    o = tslb.tslb_default_options()
+    full = tslb.tslb_workspace_bytes(g, o)
+    o.closure = tslb.CLOSURES["chapman_enskog"]
+    ce = tslb.tslb_workspace_bytes(g, o)
+    assert 2 * 5 * N * 4 <= ce and full - ce >= 2 * 6 * N * 4
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """Offsets and sizes of the option, boundary and grid structs as gcc lays
+    them out from the header, against the binding's ctypes structures."""
+    structs = {"tslb_options": tslb.Options, "tslb_boundary": tslb.Boundary, "tslb_grid": tslb.Grid}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "tslb.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
