@@ -27,6 +27,7 @@ struct Instance {
     double* avg = nullptr;  // time sums of phi and u_z (option `average`)
     int tile_begin = 0, tile_end = 0;  // batch: its tiles in the tile list
     bool set = false;
+    tslb::TileMaps maps[2] = {};       // TMA tensor maps of the steps from buf[q] (made on first use)
 };
 
 }  // namespace
@@ -240,12 +241,13 @@ bool is_device_ptr(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Tiles of one grid for a block of `nw` warps and slabs of `tile_z` planes.
-int tiles_of(const StepParams& p, int nw, int tile_z) {
+// Tiles of one grid for a block of `nw` warps and slabs of `tile_z` planes
+// (the tile width depends on the storage type).
+int tiles_of(const StepParams& p, int storage, int nw, int tile_z) {
     StepParams q = p;
     q.block_warps = nw;
     q.tile_z = std::min(tile_z, p.nz);
-    const tslb::LaunchShape sh = tslb::step_shape(q, 0);
+    const tslb::LaunchShape sh = tslb::step_shape(q, storage);
     return (int)(sh.grid.x * sh.grid.y * sh.grid.z);
 }
 
@@ -272,7 +274,7 @@ Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, b
         if (average) off += align256(2 * (size_t)p.fstride * sizeof(double));
         maxf = std::max(maxf, p.fstride);
         if (batch)
-            tiles += tiles_of(p, 8, std::min(p.tile_z, kMinTileZ));
+            tiles += tiles_of(p, storage, 8, std::min(p.tile_z, kMinTileZ));
         else
             tiles = std::max(tiles, tslb::max_partials(p, storage));
         conv = std::max(conv, tslb::max_partials(p, storage));
@@ -362,8 +364,14 @@ cudaError_t launch_one(tslb_ctx* c, int q) {
     }
     if (!c->batch) {
         Instance& I = c->inst[0];
+        tslb::TileMaps& m = I.maps[q];
+        if (m.block_warps != I.p.block_warps) {  // boxes are shaped for one block size
+            cudaError_t e = tslb::make_tile_maps(I.p, c->storage, I.buf[q], I.buf[q ^ 1], &m);
+            if (e != cudaSuccess) return e;
+            m.block_warps = I.p.block_warps;
+        }
         return tslb::launch_step(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
-                                 c->partials, c->stream);
+                                 c->partials, c->stream, &m);
     }
     return tslb::launch_batch_step(c->batch_nw, c->dinst, c->dtiles, c->ntiles, q, c->tdev + q, c->tdev + (q ^ 1),
                                    c->counters, c->partials, c->sms, c->stream);
@@ -414,7 +422,7 @@ tslb_status finish_sums(tslb_ctx* c, int i, double* mass, double* phi_total) {
         } else if (c->scheme == 1) {
             n = tslb::twosweep_partials(I.p);
         } else {
-            n = tiles_of(I.p, I.p.block_warps, I.p.tile_z);
+            n = tiles_of(I.p, c->storage, I.p.block_warps, I.p.tile_z);
         }
     } else {
         double* sp = c->partials + 2 * (size_t)c->max_tiles;
@@ -423,8 +431,11 @@ tslb_status finish_sums(tslb_ctx* c, int i, double* mass, double* phi_total) {
     }
     CK(tslb::launch_finish_sums(parts, n, c->result, c->stream), "sum reduction");
     double r[2];
+    int err = 0;
     CK(cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream), "sums copy");
+    CK(cudaMemcpyAsync(&err, c->counters + 2, sizeof(err), cudaMemcpyDeviceToHost, c->stream), "error word copy");
     CK(cudaStreamSynchronize(c->stream), "sums synchronise");
+    if (err) return bad(c, "a step kernel gave up waiting for its tile data (bounded wait expired)", TSLB_ERR_TIMEOUT);
     *mass = (double)I.N + r[0];
     *phi_total = r[1];
     if (!std::isfinite(*mass) || !std::isfinite(*phi_total))
@@ -569,7 +580,8 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
     c->max_tiles = L.max_tiles;
     c->result = reinterpret_cast<double*>(base + L.result);
     c->tdev = reinterpret_cast<long long*>(base + L.tdev);
-    c->counters = reinterpret_cast<int*>(base + L.counters);
+    c->counters = reinterpret_cast<int*>(base + L.counters);  // [0..1] batch tile counters, [2] error word
+    for (Instance& I : c->inst) I.p.err = c->counters + 2;
     c->dinst = reinterpret_cast<tslb::BatchInstance*>(base + L.dinst);
     c->dtiles = reinterpret_cast<int4*>(base + L.dtiles);
     if (c->scheme == 1) {
@@ -836,9 +848,10 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     if (c->scheme == 1) return bad(c, "the two-sweep scheme has no tile shape to tune");
     CK(cudaSetDevice(c->device), "set device");
     const int q = c->cur;
-    const int warps_single[] = {8, 12};
-    const int warps_batch[] = {8, 12};
-    const int* warps = c->batch ? warps_batch : warps_single;
+    // block sizes tried (16-warp blocks of the projection step for single grids only)
+    const bool ce = !c->batch && c->inst[0].p.closure == tslb::CL_CHAPMAN_ENSKOG;
+    std::vector<int> shapes = {8, 12};
+    if (!ce && !c->batch) shapes.push_back(16);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event create");
     CK(cudaEventCreate(&e1), "event create");
@@ -847,18 +860,19 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     // the trial steps must not add to the time sums
     for (Instance& I : c->inst) I.p.avg = nullptr;
     float best = 1e30f;
-    int best_nw = c->batch ? c->batch_nw : c->inst[0].p.block_warps, best_tz = keep_tz[0];
+    int best_nw = c->batch ? c->batch_nw : c->inst[0].p.block_warps;
+    int best_tz = keep_tz[0];
     tslb_status st = TSLB_OK;
-    for (int wi = 0; wi < 2 && st == TSLB_OK; ++wi)
+    for (size_t si = 0; si < shapes.size() && st == TSLB_OK; ++si)
         for (int tz : kAutotuneTileZ) {
             // each trial re-runs the step from the current state into the other
             // buffer, so the state itself does not advance
             for (Instance& I : c->inst) {
-                I.p.block_warps = warps[wi];
+                I.p.block_warps = shapes[si];
                 I.p.tile_z = std::min(tz, I.p.nz);
             }
             if (c->batch) {
-                c->batch_nw = warps[wi];
+                c->batch_nw = shapes[si];
                 if ((st = upload_batch(c)) != TSLB_OK) break;
             }
             cudaError_t e = launch_one(c, q);
@@ -874,7 +888,7 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
             }
             if (ms < best) {
                 best = ms;
-                best_nw = warps[wi];
+                best_nw = shapes[si];
                 best_tz = tz;
             }
         }

@@ -92,6 +92,85 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ------------------------------------------------- TMA tile loads (sm_90+)
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Makes mbarrier initialisation visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// Orders this thread's view of shared memory (generic proxy) before its
+// subsequent bulk copies (async proxy) into the same memory.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of phase `parity` of an mbarrier: gives up
+// (returns false) after about kWaitCycles SM cycles (~1 s) instead of spinning
+// forever if the copies it counts never arrive.
+constexpr long long kWaitCycles = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+// Tiled bulk tensor copies global -> shared memory, completing on `bar`.
+// Coordinates are element indices, innermost first; the innermost one must
+// be a multiple of 16 bytes (the callers align it down).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int f,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(f), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Tiled bulk tensor copy shared -> global memory (4D), in the calling
+// thread's bulk async-group; elements outside the tensor are not written.
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int x, int y, int z, int f) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n" ::"l"(
+            reinterpret_cast<unsigned long long>(map)),
+        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z), "r"(f)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// Waits until at most N bulk groups of this thread still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+// Waits until at most N bulk groups of this thread are still in flight.
+template <int N>
+__device__ __forceinline__ void bulk_wait() {
+    asm volatile("cp.async.bulk.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Stored <-> FP32 conversion of one field value.
 template <typename S>
 struct Io;
@@ -99,6 +178,7 @@ template <>
 struct Io<float> {
     static constexpr bool kAsync = true;
     static __device__ __forceinline__ float from_raw(unsigned short, float) { return 0.f; }
+    static __device__ __forceinline__ float cvt(float v, float) { return v; }
     static __device__ __forceinline__ float ld(const float* p, float) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
     static __device__ __forceinline__ float round_trip(float v, float, float) { return v; }
@@ -109,6 +189,7 @@ struct Io<__half> {
     static __device__ __forceinline__ float from_raw(unsigned short r, float inv) {
         return __half2float(__ushort_as_half(r)) * inv;
     }
+    static __device__ __forceinline__ float cvt(__half v, float inv) { return __half2float(v) * inv; }
     static __device__ __forceinline__ float ld(const __half* p, float inv) { return __half2float(__ldg(p)) * inv; }
     static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
     static __device__ __forceinline__ float round_trip(float v, float s, float inv) {
@@ -121,6 +202,7 @@ struct Io<__nv_bfloat16> {
     static __device__ __forceinline__ float from_raw(unsigned short r, float inv) {
         return __bfloat162float(__ushort_as_bfloat16(r)) * inv;
     }
+    static __device__ __forceinline__ float cvt(__nv_bfloat16 v, float inv) { return __bfloat162float(v) * inv; }
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p, float inv) {
         return __bfloat162float(__ldg(p)) * inv;
     }
@@ -212,6 +294,63 @@ __device__ __forceinline__ void interface2(const float* zb, int lane, int w, flo
     }
     const int ec = (lane + 1) + PHX * (2 * w + 1);
     phi = make_float2(zb[ec], zb[ec + PHX]);
+    const float2 gxp = (1.f / 72.f) * (yS[2] - yS[0]);
+    const float2 gyp = (1.f / 72.f) * s0v(yDS[0], yDS[1], yDS[2]);
+    const float2 gzp = (1.f / 72.f) * s0v(ySD[0], ySD[1], ySD[2]);
+    const float2 hxx = (1.f / 36.f) * l2v(yS[0], yS[1], yS[2]);
+    const float2 hyy = (1.f / 36.f) * s0v(yLS[0], yLS[1], yLS[2]);
+    const float2 hzz = (1.f / 36.f) * s0v(ySL[0], ySL[1], ySL[2]);
+    const float2 hxy = (1.f / 24.f) * (yDS[2] - yDS[0]);
+    const float2 hxz = (1.f / 24.f) * (ySD[2] - ySD[0]);
+    const float2 hyz = (1.f / 24.f) * s0v(yDD[0], yDD[1], yDD[2]);
+
+    const float2 m2 = mad(gxp, gxp, mad(gyp, gyp, mad(gzp, gzp, bc(eps2))));
+    const float2 im = make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
+    nxv = gxp * im;
+    nyv = gyp * im;
+    nzv = gzp * im;
+    const float2 ghg = mad(gxp, mad(gxp, hxx, 2.f * mad(gyp, hxy, gzp * hxz)),
+                           mad(gyp, mad(gyp, hyy, 2.f * (gzp * hyz)), gzp * gzp * hzz));
+    const float2 kappa = (hxx + hyy + hzz) * im - ghg * (im * im * im);
+    const float2 fk = sig_half * kappa;
+    Fx = fk * gxp;
+    Fy = fk * gyp;
+    Fz = fk * gzp;
+}
+
+// Interface terms of the staged row pair as interface2, from z combinations
+// stored per phase-field element as float4 {S, D, L, phi} with
+// S = 4 phi + (phi(z+1) + phi(z-1)), D = phi(z+1) - phi(z-1),
+// L = (phi(z+1) + phi(z-1)) - 2 phi: one 16-byte load per element, the y
+// combinations of the two rows in scalar arithmetic (their operands come from
+// four different rows, so packing them would cost register moves), the x
+// combinations and the rest in packed FP32.  The arithmetic is that of
+// interface2, operation for operation.
+template <int NPH>
+__device__ __forceinline__ void interface4(const float4* zb, int lane, int w, float sig_half, float eps2,
+                                           float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
+                                           float2& nyv, float2& nzv) {
+    float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+        float zS[4], zD[4], zL[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 v = zb[(lane + 1 + dx) + PHX * (2 * w + r)];
+            zS[r] = v.x;
+            zD[r] = v.y;
+            zL[r] = v.z;
+            if (dx == 0 && r == 1) phi.x = v.w;
+            if (dx == 0 && r == 2) phi.y = v.w;
+        }
+        const int k = dx + 1;
+        yS[k] = make_float2(fmaf(4.f, zS[1], zS[0] + zS[2]), fmaf(4.f, zS[2], zS[1] + zS[3]));
+        yDS[k] = make_float2(zS[2] - zS[0], zS[3] - zS[1]);
+        yLS[k] = make_float2(fmaf(-2.f, zS[1], zS[0] + zS[2]), fmaf(-2.f, zS[2], zS[1] + zS[3]));
+        ySD[k] = make_float2(fmaf(4.f, zD[1], zD[0] + zD[2]), fmaf(4.f, zD[2], zD[1] + zD[3]));
+        yDD[k] = make_float2(zD[2] - zD[0], zD[3] - zD[1]);
+        ySL[k] = make_float2(fmaf(4.f, zL[1], zL[0] + zL[2]), fmaf(4.f, zL[2], zL[1] + zL[3]));
+    }
     const float2 gxp = (1.f / 72.f) * (yS[2] - yS[0]);
     const float2 gyp = (1.f / 72.f) * s0v(yDS[0], yDS[1], yDS[2]);
     const float2 gzp = (1.f / 72.f) * s0v(ySD[0], ySD[1], ySD[2]);

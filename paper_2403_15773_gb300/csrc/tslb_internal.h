@@ -2,6 +2,7 @@
 // kernels (tslb_step.cu) of the TSLB library.  Not installed, not part of the ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,6 +42,21 @@ struct StepParams {
     float scale[NFIELDS];    // 16-bit storage: stored = scale * value
     float inv_scale[NFIELDS];
     double* avg;             // time sums of phi and u_z (2 blocks of fstride doubles) or null
+    int* err;                // set to 1 by a kernel whose bounded wait for its tile data gave up
+};
+
+// Tensor maps of one step for the TMA tile copies of the step kernel: the 10
+// moment fields of the input buffer as a 4D tensor {nx, ny, nz, field}, its
+// phase field as a 3D tensor {nx, ny, nz}, and (FP32) the 11 fields of the
+// output buffer, with the box shapes of the block size they were made for.
+// valid = 0: every tile loads element by element; store = 0: plain stores.
+struct TileMaps {
+    CUtensorMap mom;
+    CUtensorMap phi;
+    CUtensorMap out;
+    int valid;
+    int store;
+    int block_warps;
 };
 
 // One grid of a batch: its parameters and its two state buffers.
@@ -60,9 +76,16 @@ LaunchShape step_shape(const StepParams& p, int storage);
 
 // One time step: state `in` (step index *t_in) -> state `out` (*t_out = *t_in + 1),
 // per-block FP64 partial sums (sum rho, sum phi) into partials[2 * block].
+// maps: tensor maps of `in` (TMA tile loads when maps->valid and made for
+// p.block_warps), or null.
 cudaError_t launch_step(const StepParams& p, int storage, const void* in, void* out,
                         const long long* t_in, long long* t_out, double* partials,
-                        cudaStream_t s);
+                        cudaStream_t s, const TileMaps* maps = nullptr);
+
+// Encodes the tensor maps of a step from state buffer `in` to `out` for
+// blocks of p.block_warps warps (maps->valid = 0 where TMA cannot address the
+// layout: rows not a multiple of 16 bytes).  Host only; needs no device work.
+cudaError_t make_tile_maps(const StepParams& p, int storage, const void* in, const void* out, TileMaps* maps);
 
 // Kernel attributes (dynamic shared memory) of the step kernel; once per device.
 cudaError_t prepare_kernels(int storage);
@@ -92,12 +115,12 @@ cudaError_t launch_finish_sums(const double* partials, int n, double* result, cu
 int max_partials(const StepParams& p, int storage);
 
 // Batched FP32 step: tiles[k] = (instance, bx, by, bz) over all instances,
-// taken from counters[parity] by `nblocks` persistent blocks of `nw` warps
-// (8 or 12); tile k writes partials[2k..2k+1].
+// taken from counters[parity] by one persistent block per SM on `sms` SMs,
+// blocks of `nw` warps (8 or 12); tile k writes partials[2k..2k+1].
 cudaError_t prepare_batch_kernels();
 cudaError_t launch_batch_step(int nw, const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
                               const long long* t_in, long long* t_out, int* counters, double* partials,
-                              int nblocks, cudaStream_t s);
+                              int sms, cudaStream_t s);
 
 // The paper's two-sweep design (ablation): collide+push of the moments M into
 // 34 population arrays `pops` (27 f_i - w_i, then 7 g_k), then the moments of

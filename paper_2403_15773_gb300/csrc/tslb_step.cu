@@ -34,6 +34,8 @@
 //
 // All arithmetic is FP32 and works with deviations from the rest state
 // (rho - 1, Pi - cs2 I) so that no O(1) terms cancel.
+#include <cstring>
+
 #include "tslb_device.cuh"
 
 namespace tslb {
@@ -41,36 +43,86 @@ namespace {
 
 // ----------------------------------------------------- step kernel (pairs)
 
-template <int NW>
+// Shared memory of a block of NW warps with storage type S.  The moment and
+// phase-field planes of a tile are held as the boxes a TMA copy writes: a
+// moment box is [10 fields][NR rows][MW columns], a phase-field box
+// [NR + 2 rows][PW columns], each starting at the staged tile's first column
+// rounded down to 16 bytes (offsets offm / offp inside the box).
+template <int NW, typename S>
 struct Step2Smem {
-    static constexpr int NT = 32 * NW;              // threads
-    static constexpr int NR = 2 * NW;               // staged rows (two per warp)
-    static constexpr int NS = 32 * NR;              // staged nodes
-    static constexpr int NPH = PHX * (NR + 2);      // phase-field elements (halo 2)
-    static constexpr int RING = 0;                  // [4][NPH] phase-field planes
-    static constexpr int ZC = RING + 4 * NPH;       // [2][3][NPH] z combinations of phi
-    static constexpr int MOM = ZC + 6 * NPH;        // [2][10][NS] staged moments
-    static constexpr int YX = MOM + 20 * NS;        // [2][20][NT] y exchange
-    static constexpr int FLOATS = YX + 40 * NT;
-    static constexpr size_t BYTES = sizeof(float) * FLOATS;
+    static constexpr int NT = 32 * NW;                       // threads
+    static constexpr int NR = 2 * NW;                        // staged rows (two per warp)
+    static constexpr int TY = NR - 2;                        // interior rows
+    static constexpr int NPH = PHX * (NR + 2);               // phase-field elements (halo 2)
+    static constexpr int AL = 16 / (int)sizeof(S);           // elements per 16 bytes
+    // interior columns of a tile: FP32 tiles start on 16-byte boundaries (28
+    // columns) so that finished planes leave by TMA store; 16-bit tiles are 30
+    // wide (a 16-byte store box would be 24 columns) and use plain stores
+    static constexpr bool kFp32 = sizeof(S) == 4;
+    static constexpr int TXS = kFp32 ? 28 : 30;
+    // (16-warp blocks have no room for the staging boxes: plain stores)
+    static constexpr bool kTmaStore = kFp32 && NW <= 12;
+    // box columns: staged columns x0-1 .. x0+30 (moments) and x0-2 .. x0+31
+    // (phase field) from the 16-byte boundary below them
+    static constexpr int MW = kFp32 ? 36 : 40;
+    static constexpr int PW = kFp32 ? 36 : 40;
+    static constexpr int MAXOFFM = kFp32 ? 3 : 7, MAXOFFP = kFp32 ? 2 : 6;
+    static constexpr int FS = NR * MW;                       // elements between fields of a moment box
+    static constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
+    static constexpr size_t MOM_BOX = sizeof(S) * 10 * FS;           // bytes of one moment box
+    static constexpr size_t PHI_BOX = sizeof(S) * (NR + 2) * PW;     // bytes of one phase-field box
+    static constexpr size_t MOM_SLOT = r128(MOM_BOX), PHI_SLOT = r128(PHI_BOX);
+    // planes between the load of a plane's moments and their use (the phase
+    // field is loaded two planes further ahead); 16 warps: shared memory
+    // holds one plane less
+    static constexpr int PF = NW <= 8 ? 2 : 1;
+    static constexpr int MS = PF + 1, PS = PF + 3, NB = PF + 2;      // moment slots, phase slots, mbarriers
+    static constexpr size_t MOM = 0;                                 // [MS] moment boxes
+    static constexpr size_t RING = MOM + MS * MOM_SLOT;              // [PS] phase-field boxes
+    static constexpr size_t ZC = RING + PS * PHI_SLOT;               // [NPH] float4 z combinations
+    static constexpr size_t YX = ZC + 16 * (size_t)NPH;              // [20][NT] float y exchange
+    static constexpr size_t OUT_BOX = kTmaStore ? sizeof(float) * NFIELDS * TY * TXS : 0;  // [11][TY][TXS]
+    static constexpr size_t OUT_SLOT = r128(OUT_BOX);
+    static constexpr size_t OUT = r128(YX + sizeof(float) * 20 * NT);  // [2] output staging boxes
+    static constexpr size_t BAR = OUT + 2 * OUT_SLOT;                 // NB mbarriers
+    static constexpr size_t BYTES = BAR + NB * sizeof(uint64_t) + 128;  // + alignment slack of the base
+    static_assert(MAXOFFM + 32 <= MW && MAXOFFP + PHX <= PW, "box too narrow for the aligned tile");
+    static_assert(!kTmaStore || (TXS * sizeof(S)) % 16 == 0, "store box rows must be 16-byte multiples");
+    static_assert(BYTES <= 227 * 1024, "more shared memory than a block can have");
 };
+
+__device__ __forceinline__ unsigned char* align128(unsigned char* p) {
+    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
+}
 
 // One tile of one time step: the 30 x (2 NW - 2) interior columns at tile
 // (bx, by), planes [bz * tile_z, (bz + 1) * tile_z), from state `in` (step t)
 // to state `out`; writes the tile's FP64 partial sums to part[0..1].
+// maps: tensor maps of `in` for TMA loads, or null (element-wise loads).
 template <int NW, typename S>
-__device__ __forceinline__ void step_tile(const StepParams& P, const S* __restrict__ in, S* __restrict__ out,
-                                          const long long t, const int bx, const int by, const int bz,
-                                          double* __restrict__ part) {
-    using L = Step2Smem<NW>;
-    constexpr int NT = L::NT, NR = L::NR, NS = L::NS, NPH = L::NPH;
-    constexpr int TY = NR - 2;
+__device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
+                                          S* __restrict__ out, const long long t, const int bx, const int by,
+                                          const int bz, double* __restrict__ part) {
+    using L = Step2Smem<NW, S>;
+    constexpr int NT = L::NT, NR = L::NR, NPH = L::NPH, MW = L::MW, PW = L::PW, FS = L::FS, AL = L::AL;
+    constexpr int TY = L::TY, TX = L::TXS;
+    constexpr int OSL = (int)(L::OUT_SLOT / sizeof(float));
     constexpr int EPT = (NPH + NT - 1) / NT;
-    extern __shared__ __align__(16) float smem[];
-    float* const ring = smem + L::RING;
-    float* const zc = smem + L::ZC;
-    float* const mom = smem + L::MOM;
-    float* const yx = smem + L::YX;
+    constexpr int MSL = (int)(L::MOM_SLOT / sizeof(S)), PSL = (int)(L::PHI_SLOT / sizeof(S));
+    constexpr int PF = L::PF, MS = L::MS, PS = L::PS, NB = L::NB;
+    // slots of plane q (q >= -2) and the mbarrier of the loads issued at iteration i (>= -1)
+    auto mslot = [](int q) { return (q + 12) % MS; };
+    auto pslot = [](int q) { return (q + 20) % PS; };
+    auto bslot = [](int i) { return (i + 12) % (PF + 1); };
+    constexpr int BPRO = PF + 1;  // mbarrier of the prologue loads
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* const sm = align128(smem_raw);
+    S* const momb = reinterpret_cast<S*>(sm + L::MOM);
+    S* const ring = reinterpret_cast<S*>(sm + L::RING);
+    float4* const zc = reinterpret_cast<float4*>(sm + L::ZC);
+    float* const yx = reinterpret_cast<float*>(sm + L::YX);
+    float* const outb = reinterpret_cast<float*>(sm + L::OUT);
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
 
     const int lane = threadIdx.x, w = threadIdx.y, tid = lane + 32 * w;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
@@ -78,6 +130,18 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
     const long long fs = P.fstride;
     const int x0 = bx * TX, y0 = by * TY, z0 = bz * P.tile_z;
     const int z1 = min(z0 + P.tile_z, nz);
+    const bool use_maps = maps != nullptr && maps->valid && maps->block_warps == NW;
+    // finished planes leave through the staging box by TMA store (FP32)
+    const bool tst = L::kTmaStore && use_maps && maps->store;
+    if (use_maps && tid == 0) {
+        for (int k = 0; k < NB; ++k) mbar_init(bar + k, 1);
+        fence_mbar_init();
+    }
+
+    // box origins (x aligned down to 16 bytes; floor for negative x)
+    const int xm = (x0 - 1) & ~(AL - 1), xp = (x0 - 2) & ~(AL - 1);
+    const int ym = y0 - 1, yp = y0 - 2;
+    const int offm = x0 - 1 - xm, offp = x0 - 2 - xp;
 
     // the two staged nodes of this thread (constant along the march)
     int unused = 0;
@@ -90,101 +154,201 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
     const bool col_ok = lane >= 1 && lane <= TX && gx < nx;
     const bool storeA = col_ok && w >= 1 && gyA < ny;       // staged row 2w is interior for w >= 1
     const bool storeB = col_ok && w <= NW - 2 && gyB < ny;  // staged row 2w+1 for w <= NW-2
-    const int sA = lane + 64 * w;                           // staged-node slot of row 2w (row 2w+1: +32)
 
-    int pxy[EPT];
+    // Where each staged value is read in shared memory: at its own box position
+    // (element-wise loads fetch the ghost-resolved source into it), or, for TMA
+    // tiles, at the box position of its resolved source (ghost images of
+    // mirror and copy faces lie inside the box; a tile whose sources do not,
+    // e.g. across a periodic wrap, loads element-wise).
+    // Staged values beyond the ghost layers a stencil reaches (ragged tiles)
+    // feed no stored node: they keep their own position.
+    int mrdA = (2 * w) * MW + lane + offm, mrdB = mrdA + MW;
+    const bool usex = gx >= -1 && gx <= nx, useA = usex && gyA >= -1 && gyA <= ny, useB = usex && gyB >= -1 && gyB <= ny;
+    const int resA = useA ? (syA - ym) * MW + (sx - xm) : mrdA, resB = useB ? (syB - ym) * MW + (sx - xm) : mrdB;
+    bool inbox = (!useA || (sx >= xm && sx - xm < MW && syA >= ym && syA - ym < NR)) &&
+                 (!useB || (sx >= xm && sx - xm < MW && syB >= ym && syB - ym < NR));
+    int pxy[EPT], prd[EPT], pres[EPT];
     float phib[EPT];
-    const bool inlet_planes = P.face[4] == BC_INLET && z0 < 2;
+    const bool inlet_face = P.face[4] == BC_INLET;
+    const bool inlet_planes = inlet_face && z0 < 2;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
         const int idx = tid + e * NT;
         pxy[e] = 0;
+        prd[e] = pres[e] = 0;
         phib[e] = 0.f;
         if (idx < NPH) {
             float sg;
-            const int psx = resolve_axis(x0 - 2 + idx % PHX, nx, P.face[0], P.face[1], sg, unused);
-            const int psy = resolve_axis(y0 - 2 + idx / PHX, ny, P.face[2], P.face[3], sg, unused);
+            const int r = idx / PHX, c = idx % PHX;
+            const int psx = resolve_axis(x0 - 2 + c, nx, P.face[0], P.face[1], sg, unused);
+            const int psy = resolve_axis(y0 - 2 + r, ny, P.face[2], P.face[3], sg, unused);
+            const int gxe = x0 - 2 + c, gye = y0 - 2 + r;
+            const bool used = gxe >= -2 && gxe <= nx + 1 && gye >= -2 && gye <= ny + 1;
             pxy[e] = psx + nx * psy;
+            prd[e] = r * PW + c + offp;
+            pres[e] = used ? (psy - yp) * PW + (psx - xp) : prd[e];
+            inbox = inbox && (!used || (psx >= xp && psx - xp < PW && psy >= yp && psy - yp < NR + 2));
             if (inlet_planes) phib[e] = inlet_phi(P, psx, psy);
         }
     }
+    const bool tma = __syncthreads_and(use_maps && inbox) != 0;
+    if (tma) {
+        mrdA = resA;
+        mrdB = resB;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) prd[e] = pres[e];
+    }
 
-    // FP32: cp.async straight into shared memory, one plane ahead.  16-bit
-    // storage: the next plane's raw values wait in registers while the
-    // current plane is computed and are widened into the same shared-memory
-    // slots afterwards (each slot is read only by the thread that fills it).
+    // Loads of the phase field at plane qp (if do_p) and the moments at plane
+    // qm (if do_m) into their ring / moment slots.  TMA: one thread posts the
+    // byte count on mbarrier kb and issues the box copies.  Element-wise: FP32
+    // cp.async straight into shared memory; 16-bit values wait in registers
+    // until commit().  Inlet planes of the phase field are never loaded (the
+    // imposed values are used directly).  Returns whether bar[kb] got copies.
     unsigned short rphi[EPT], rmom[2][10];
-    int rphi_inl = 0;
-    auto issue_phi = [&](int q) {
+    auto issue = [&](bool do_p, int qp, bool do_m, int qm, int kb, float& sgz, int& inl) -> bool {
         float sg;
-        int inl = 0;
-        const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);
-        float* dst = ring + ((q + 8) & 3) * NPH;
-        const S* src = in + F_PHI * fs + nxy * sz;
-        rphi_inl = inl;
+        int inl_p = 0;
+        const int szp = do_p ? resolve_axis(qp, nz, P.face[4], P.face[5], sg, inl_p) : 0;
+        inl = 0;
+        sgz = 1.f;
+        const int szm = do_m ? resolve_axis(qm, nz, P.face[4], P.face[5], sgz, inl) : 0;
+        const bool lp = do_p && !inl_p;
+        S* const pdst = ring + pslot(qp) * PSL;
+        S* const mdst = momb + mslot(qm) * MSL;
+        if (tma) {
+            if (tid == 0 && (lp || do_m)) {
+                fence_proxy_async();
+                mbar_expect_tx(bar + kb, (lp ? (unsigned)L::PHI_BOX : 0u) + (do_m ? (unsigned)L::MOM_BOX : 0u));
+                if (lp) tma_load_3d(pdst, &maps->phi, xp, yp, szp, bar + kb);
+                if (do_m) tma_load_4d(mdst, &maps->mom, xm, ym, szm, 0, bar + kb);
+            }
+            return lp || do_m;
+        }
+        if (lp) {
+            const S* src = in + F_PHI * fs + nxy * szp;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e)
+                if (tid + e * NT < NPH) {
+                    if constexpr (Io<S>::kAsync)
+                        cp_async4(reinterpret_cast<float*>(pdst + prd[e]), reinterpret_cast<const float*>(src + pxy[e]));
+                    else
+                        rphi[e] = __ldg(reinterpret_cast<const unsigned short*>(src + pxy[e]));
+                }
+        }
+        if (do_m) {
+            const S* srcA = in + nxy * szm + sxyA;
+            const S* srcB = in + nxy * szm + sxyB;
+#pragma unroll
+            for (int f = 0; f < 10; ++f) {
+                if constexpr (Io<S>::kAsync) {
+                    cp_async4(reinterpret_cast<float*>(mdst + mrdA + f * FS), reinterpret_cast<const float*>(srcA + f * fs));
+                    cp_async4(reinterpret_cast<float*>(mdst + mrdB + f * FS), reinterpret_cast<const float*>(srcB + f * fs));
+                } else {
+                    rmom[0][f] = __ldg(reinterpret_cast<const unsigned short*>(srcA + f * fs));
+                    rmom[1][f] = __ldg(reinterpret_cast<const unsigned short*>(srcB + f * fs));
+                }
+            }
+        }
+        return false;
+    };
+    // 16-bit element-wise loads: registers -> shared memory (raw values).
+    auto commit = [&](bool do_p, int qp, bool do_m, int qm) {
+        if constexpr (!Io<S>::kAsync) {
+            if (tma) return;
+            if (do_p && !(inlet_face && qp < 0)) {
+                unsigned short* dst = reinterpret_cast<unsigned short*>(ring + pslot(qp) * PSL);
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    if (tid + e * NT < NPH) dst[prd[e]] = rphi[e];
+            }
+            if (do_m) {
+                unsigned short* dst = reinterpret_cast<unsigned short*>(momb + mslot(qm) * MSL);
+#pragma unroll
+                for (int f = 0; f < 10; ++f) {
+                    dst[mrdA + f * FS] = rmom[0][f];
+                    dst[mrdB + f * FS] = rmom[1][f];
+                }
+            }
+        }
+    };
+    unsigned pend = 0, phase = 0;  // mbarriers with copies in flight; their phase parities
+    bool dead = false;             // a bounded wait gave up: finish the tile without further waits
+    auto wait_bar = [&](int kb) {
+        if (!((pend >> kb) & 1u)) return;
+        if (!dead && !mbar_wait(bar + kb, (phase >> kb) & 1u)) {
+            dead = true;
+            if (P.err) *P.err = 1;
+        }
+        phase ^= 1u << kb;
+        pend &= ~(1u << kb);
+    };
+    // z combinations {S, D, L, phi} of the phase field at plane q from the
+    // ring planes q - 1, q, q + 1 (see interface4); inlet planes are imposed
+    auto zcombine = [&](int q) {
+        const S* pm = ring + pslot(q - 1) * PSL;
+        const S* pc = ring + pslot(q) * PSL;
+        const S* pp = ring + pslot(q + 1) * PSL;
+        const bool im = inlet_face && q - 1 < 0, ic = inlet_face && q < 0;
+        const float inv = P.inv_scale[F_PHI];
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const int idx = tid + e * NT;
             if (idx < NPH) {
-                if (inl) {
-                    dst[idx] = phib[e];
-                } else if constexpr (Io<S>::kAsync) {
-                    cp_async4(dst + idx, reinterpret_cast<const float*>(src + pxy[e]));
-                } else {
-                    rphi[e] = __ldg(reinterpret_cast<const unsigned short*>(src + pxy[e]));
-                }
-            }
-        }
-    };
-    auto commit_phi = [&](int q) {
-        if constexpr (!Io<S>::kAsync) {
-            if (!rphi_inl) {
-                float* dst = ring + ((q + 8) & 3) * NPH;
-#pragma unroll
-                for (int e = 0; e < EPT; ++e) {
-                    const int idx = tid + e * NT;
-                    if (idx < NPH) dst[idx] = Io<S>::from_raw(rphi[e], P.inv_scale[F_PHI]);
-                }
-            }
-        }
-    };
-    auto issue_mom = [&](int q, float& sgz, int& inl) {
-        inl = 0;
-        const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sgz, inl);
-        float* dst = mom + ((q + 8) & 1) * 10 * NS + sA;
-        const S* srcA = in + nxy * sz + sxyA;
-        const S* srcB = in + nxy * sz + sxyB;
-#pragma unroll
-        for (int f = 0; f < 10; ++f) {
-            if constexpr (Io<S>::kAsync) {
-                cp_async4(dst + f * NS, reinterpret_cast<const float*>(srcA + f * fs));
-                cp_async4(dst + f * NS + 32, reinterpret_cast<const float*>(srcB + f * fs));
-            } else {
-                rmom[0][f] = __ldg(reinterpret_cast<const unsigned short*>(srcA + f * fs));
-                rmom[1][f] = __ldg(reinterpret_cast<const unsigned short*>(srcB + f * fs));
-            }
-        }
-    };
-    auto commit_mom = [&](int q) {
-        if constexpr (!Io<S>::kAsync) {
-            float* dst = mom + ((q + 8) & 1) * 10 * NS + sA;
-#pragma unroll
-            for (int f = 0; f < 10; ++f) {
-                dst[f * NS] = Io<S>::from_raw(rmom[0][f], P.inv_scale[f]);
-                dst[f * NS + 32] = Io<S>::from_raw(rmom[1][f], P.inv_scale[f]);
+                const float a = im ? phib[e] : Io<S>::cvt(pm[prd[e]], inv);
+                const float b = ic ? phib[e] : Io<S>::cvt(pc[prd[e]], inv);
+                const float c = Io<S>::cvt(pp[prd[e]], inv);
+                const float s = c + a;
+                zc[idx] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
             }
         }
     };
 
-    float sgz_cur, sgz_nxt;
-    int inl_cur, inl_nxt;
-    for (int q = z0 - 2; q <= z0 + 1; ++q) {
-        issue_phi(q);
-        commit_phi(q);
+    // prologue: phase field at planes z0-2 .. z0+PF, moments at planes z0-1 .. z0+PF-2
+    float sgz_cur = 1.f, sgz_nxt = 1.f;
+    int inl_cur = 0, inl_nxt = 0;
+    if (tma) {
+        float sg;
+        int inl;
+        unsigned bytes = 0;
+        for (int q = z0 - 2; q <= z0 + PF; ++q) {
+            inl = 0;
+            resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);
+            if (!inl) bytes += (unsigned)L::PHI_BOX;
+        }
+        if (tid == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(bar + BPRO, bytes + PF * (unsigned)L::MOM_BOX);
+            for (int q = z0 - 2; q <= z0 + PF; ++q) {
+                inl = 0;
+                const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);
+                if (!inl) tma_load_3d(ring + pslot(q) * PSL, &maps->phi, xp, yp, sz, bar + BPRO);
+            }
+            for (int k = 0; k < PF; ++k) {
+                const int q = z0 - 1 + k;
+                const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);
+                tma_load_4d(momb + mslot(q) * MSL, &maps->mom, xm, ym, sz, 0, bar + BPRO);
+            }
+        }
+        pend |= 1u << BPRO;
+    } else {
+        float sg;
+        int inl;
+        for (int q = z0 - 2; q <= z0 + PF; ++q) {
+            issue(true, q, false, 0, BPRO, sg, inl);
+            commit(true, q, false, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            issue(false, 0, true, z0 - 1 + k, BPRO, sg, inl);
+            commit(false, 0, true, z0 - 1 + k);
+        }
     }
-    issue_mom(z0 - 1, sgz_cur, inl_cur);
-    commit_mom(z0 - 1);
     cp_async_commit();
+    cp_async_wait<0>();
+    wait_bar(BPRO);
+    __syncthreads();
+    zcombine(z0 - 1);
 
     float2 cPP[6], cP[6], cZ[6];
 #pragma unroll
@@ -192,95 +356,148 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
     float2 cH = bc(0.f), cVPP = bc(0.f), cVP = bc(0.f);
     float sum_rho = 0.f, sum_phi = 0.f;
 
-    // S: what stage (d) of a plane hands to stage (e) of the same plane one
-    // iteration later (y populations kept in the thread, D3Q7 x/z terms)
-    float2 sYZ[9];
-    float sPA[9], sMB[9];
-    float2 s_hx = bc(0.f), s_vzp = bc(0.f), s_vzm = bc(0.f);
-    float s_dyA = 0.f, s_dyB = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        sYZ[k] = bc(0.f);
-        sPA[k] = sMB[k] = 0.f;
-    }
-    // the first iteration's stage (e) reads a y-exchange buffer no stage (d)
-    // has written: clear both buffers
-    for (int k = tid; k < 40 * NT; k += NT) yx[k] = 0.f;
-
     const float om1 = 1.f - P.omega, fo = 1.f - 0.5f * P.omega;
     const float sig_half = -0.5f * P.sigma;
 
-    // prologue: z combinations of plane z0 - 1
-    cp_async_wait<0>();
-    {
-        const int i = z0 - 2;
-        {  // z combinations of phi at plane i + 1
-            const float* pm = ring + ((i + 8) & 3) * NPH;
-            const float* pc = ring + ((i + 1 + 8) & 3) * NPH;
-            const float* pp = ring + ((i + 2 + 8) & 3) * NPH;
-            float* z = zc + ((i + 1 + 8) & 1) * 3 * NPH;
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                const int idx = tid + e * NT;
-                if (idx < NPH) {
-                    const float a = pm[idx], b = pc[idx], c = pp[idx];
-                    z[idx] = b;
-                    z[NPH + idx] = c + a;
-                    z[2 * NPH + idx] = c - a;
-                }
-            }
+    // March over planes i = z0 - 1 .. z1 with two barriers per plane:
+    //   B: the z combinations of plane i are complete, the y exchange of the
+    //      previous plane has been read, the slots loaded next are free;
+    //   loads of phi(i + 2 + PF) and the moments of i + PF; wait for those of
+    //      phi(i + 2) and the moments of i (issued PF planes earlier);
+    //   (d) stencils, collision, x sweep and y populations of plane i;
+    //   A: the y exchange of plane i is complete;
+    //   (e) y shift and moments, z shift and moments of plane i, output of
+    //      plane i - 1; z combinations of plane i + 1 (ring planes i .. i + 2).
+    // The values (d) hands to (e) live in registers only across barrier A.
+    for (int i = z0 - 1; i <= z1; ++i) {
+        if (__syncthreads_or(dead)) break;
+        // z mirror sign and inlet flag of plane i (its moments were loaded by
+        // the prologue or PF iterations ago)
+        inl_cur = 0;
+        resolve_axis(i, nz, P.face[4], P.face[5], sgz_cur, inl_cur);
+        // plane i - 2 was staged by the previous iteration (and fenced): store it
+        if (tst && tid == 0 && i >= z0 + 2) {
+            tma_store_4d(&maps->out, outb + ((i - 2 + 8) & 1) * OSL, x0, y0, i - 2, 0);
+            bulk_commit();
         }
-
-    }
-    __syncthreads();
-
-    // Software-pipelined march, one barrier per iteration i:
-    //   (c) z combinations of plane i + 1,
-    //   (e) y / z stages of plane i - 1 (output of plane i - 2),
-    //   (d) stencils, collision and x sweep of plane i.
-    // Each shared buffer (zc, yx: two each by plane parity; the phase-field
-    // ring; the moment slots) is last read one barrier before it is rewritten.
-    for (int i = z0 - 1; i <= z1 + 1; ++i) {
-        issue_phi(i + 3);
-        issue_mom(i + 1, sgz_nxt, inl_nxt);
+        const bool do_m = i + PF <= z1, do_p = i + 2 + PF <= z1 + 1;
+        const int kb = bslot(i);
+        if ((do_m || do_p) && issue(do_p, i + 2 + PF, do_m, i + PF, kb, sgz_nxt, inl_nxt)) pend |= 1u << kb;
         cp_async_commit();
-        cp_async_wait<1>();
+        cp_async_wait<PF>();
+        wait_bar(bslot(i + 1));  // == bslot(i - PF)
 
-        {  // z combinations of phi at plane i + 1
-            const float* pm = ring + ((i + 8) & 3) * NPH;
-            const float* pc = ring + ((i + 1 + 8) & 3) * NPH;
-            const float* pp = ring + ((i + 2 + 8) & 3) * NPH;
-            float* z = zc + ((i + 1 + 8) & 1) * 3 * NPH;
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                const int idx = tid + e * NT;
-                if (idx < NPH) {
-                    const float a = pm[idx], b = pc[idx], c = pp[idx];
-                    z[idx] = b;
-                    z[NPH + idx] = c + a;
-                    z[2 * NPH + idx] = c - a;
-                }
-            }
-        }
-
-        // (e) plane i - 1: y shift and moments, z shift and moments, output of plane i - 2
+        float2 hYZ[9];
+        float hPA[9], hMB[9];
+        float2 h_hx, h_vzp, h_vzm;
+        float h_dyA, h_dyB;
+        // (d) plane i: stencils, collision, x sweep, y populations -> yx and registers
         {
-            const float* yprev = yx + ((i - 1 + 8) & 1) * 20 * NT + (w > 0 ? tid - 32 : tid);       // row 2w-1
-            const float* ynext = yx + ((i - 1 + 8) & 1) * 20 * NT + (w < NW - 1 ? tid + 32 : tid);  // row 2w+2
+            const S* mA = momb + mslot(i) * MSL + mrdA;
+            const S* mB = momb + mslot(i) * MSL + mrdB;
+            auto ld2 = [&](int f) {
+                return make_float2(Io<S>::cvt(mA[f * FS], P.inv_scale[f]), Io<S>::cvt(mB[f * FS], P.inv_scale[f]));
+            };
+            const float2 sgy = make_float2(sgyA, sgyB);
+            const float2 drho = ld2(0);
+            float2 ux = sgx * ld2(1), uy = sgy * ld2(2), uz = sgz_cur * ld2(3);
+            const float2 pxx = ld2(4), pyy = ld2(5), pzz = ld2(6);
+            const float2 pxy = (sgx * sgy) * ld2(7), pxz = (sgx * sgz_cur) * ld2(8), pyz = (sgz_cur * sgy) * ld2(9);
+            if (inl_cur) {
+                float ua[3], ub[3];
+                inlet_velocity(P, sx, syA, t, ua);
+                inlet_velocity(P, sx, syB, t, ub);
+                ux = make_float2(ua[0] * sgx, ub[0] * sgx);
+                uy = make_float2(ua[1] * sgyA, ub[1] * sgyB);
+                uz = make_float2(ua[2], ub[2]);
+            }
+
+            // interface terms from the z combinations of phi at plane i
+            float2 phi, Fx, Fy, Fz, nxv, nyv, nzv;
+            interface4<NPH>(zc, lane, w, sig_half, P.normal_eps2, phi, Fx, Fy, Fz, nxv, nyv, nzv);
+            if (inl_cur) {
+                Fx = Fy = Fz = bc(0.f);
+                nxv = nyv = nzv = bc(0.f);
+            }
+
+            // Guo forcing: v = u + F / (2 rho)
+            const float2 rho = bc(1.f) + drho;
+            const float2 irho = rcp2(rho);
+            const float2 hf = 0.5f * irho;
+            const float2 hfx = hf * Fx, hfy = hf * Fy, hfz = hf * Fz;
+            const float2 vx = ux + hfx, vy = uy + hfy, vz = uz + hfz;
+
+            // D3Q7: g_i^post = w_i (B0 + c_i . B1); x terms by shuffles, the
+            // y terms of the row pair's edges through shared memory
+            float* yb = yx + tid;
+            {
+                const float2 ga = P.gamma * (bc(1.f) - phi * phi);
+                const float2 fphi = 4.f * phi;
+                const float2 b1x = mad(fphi, vx, ga * nxv);
+                const float2 b1y = mad(fphi, vy, ga * nyv);
+                const float2 b1z = mad(fphi, vz, ga * nzv);
+                const float2 fromL = shfl_up2(phi + b1x), fromR = shfl_down2(phi - b1x);
+                h_hx = mad(0.25f, phi, 0.125f * (fromL + fromR));
+                const float2 yp2 = phi + b1y, ym2 = phi - b1y;
+                yb[18 * NT] = yp2.y;
+                yb[19 * NT] = ym2.x;
+                h_dyA = ym2.y;  // row 2w+1 -> row 2w
+                h_dyB = yp2.x;  // row 2w -> row 2w+1
+                h_vzp = phi + b1z;
+                h_vzm = phi - b1z;
+            }
+
+            // collision in Hermite form
+            const float2 nxx = pxx - rho * mad(ux, hfx, hfx * vx);
+            const float2 nyy = pyy - rho * mad(uy, hfy, hfy * vy);
+            const float2 nzz = pzz - rho * mad(uz, hfz, hfz * vz);
+            const float2 nxy = pxy - rho * mad(ux, hfy, hfx * vy);
+            const float2 nxz = pxz - rho * mad(ux, hfz, hfx * vz);
+            const float2 nyz = pyz - rho * mad(uy, hfz, hfy * vz);
+            float2 X[3][8];
+            const float2 zero = bc(0.f);
+            collide_xsweep2(rho, drho, ux, uy, uz, vx, vy, vz, Fx, Fy, Fz, nxx, nyy, nzz, nxy, nxz, nyz, om1, fo, X);
+
+            // y populations; the row pair exchanges inside the thread, the pair
+            // edges go through shared memory: p(+1) of row 2w+1 to the thread
+            // below, p(-1) of row 2w to the thread above
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int qx = 0; qx < 3; ++qx) {
+                    const float2 b0 = X[qx][3 * c], b1 = X[qx][3 * c + 1];
+                    const float2 b2 = c < 2 ? X[qx][3 * c + 2] : zero;
+                    const Tri2 tr = pops2(b0, b1, b2);
+                    const int k = 3 * qx + c;
+                    yb[(2 * k) * NT] = tr.p.y;
+                    yb[(2 * k + 1) * NT] = tr.m.x;
+                    hYZ[k] = tr.z;
+                    hPA[k] = tr.p.x;
+                    hMB[k] = tr.m.y;
+                }
+        }
+        // (e) below rewrites the staging box of plane i - 3: its store has read it
+        if (tst && tid == 0) bulk_wait_read<1>();
+        __syncthreads();
+
+        // (e) plane i: y shift and moments, z shift and moments, output of plane i - 1
+        {
+            const float* yprev = yx + (w > 0 ? tid - 32 : tid);       // row 2w-1
+            const float* ynext = yx + (w < NW - 1 ? tid + 32 : tid);  // row 2w+2
             float2 Y[3][3][3];
 #pragma unroll
             for (int qx = 0; qx < 3; ++qx)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const int k = 3 * qx + c;
-                    const float2 qp = make_float2(yprev[(2 * k) * NT], sPA[k]);
-                    const float2 qm = make_float2(sMB[k], ynext[(2 * k + 1) * NT]);
+                    const float2 qp = make_float2(yprev[(2 * k) * NT], hPA[k]);
+                    const float2 qm = make_float2(hMB[k], ynext[(2 * k + 1) * NT]);
                     const float2 s = qp + qm;
-                    Y[qx][0][c] = s + sYZ[k];
+                    Y[qx][0][c] = s + hYZ[k];
                     Y[qx][1][c] = qp - qm;
                     Y[qx][2][c] = s;
                 }
-            const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], s_dyB) + make_float2(s_dyA, ynext[19 * NT]), s_hx);
+            const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], h_dyB) + make_float2(h_dyA, ynext[19 * NT]), h_hx);
 
             const int gqx[6] = {0, 1, 0, 2, 0, 1}, gqy[6] = {0, 0, 1, 0, 2, 1};
             float2 O0[6], O1[6], O2[6];
@@ -294,12 +511,12 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
                 cP[g] = tr.p;
                 cZ[g] = tr.z;
             }
-            const float2 phin = mad(0.125f, cVPP + s_vzm, cH);
+            const float2 phin = mad(0.125f, cVPP + h_vzm, cH);
             cH = hxy;
             cVPP = cVP;
-            cVP = s_vzp;
+            cVP = h_vzp;
 
-            if (i >= z0 + 2 && i <= z1 + 1 && (storeA || storeB)) {
+            if (i >= z0 + 1 && (storeA || storeB)) {
                 const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
                 const float2 rn = bc(1.f) + dr, irn = rcp2(rn);
                 const float2 ux = jx * irn, uy = jy * irn, uz = jz * irn;
@@ -317,18 +534,34 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
                 val[F_PXZ] = O1[1] - rux * uz;
                 val[F_PYZ] = O1[2] - ruy * uz;
                 val[F_PHI] = phin;
-                const long long zo = nxy * (i - 2);
-                if (storeA) {
-                    S* o = out + zo + sxyA;
+                const long long zo = nxy * (i - 1);
+                if (tst) {  // into the staging box of plane i - 1: [field][tile row][tile column]
+                    float* ob = outb + ((i - 1 + 8) & 1) * OSL + (2 * w - 1) * TX + (lane - 1);
+                    if (storeA) {
 #pragma unroll
-                    for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
+                        for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX] = val[f].x;
+                    }
+                    if (storeB) {
+#pragma unroll
+                        for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX + TX] = val[f].y;
+                    }
+                } else {
+                    if (storeA) {
+                        S* o = out + zo + sxyA;
+#pragma unroll
+                        for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
+                    }
+                    if (storeB) {
+                        S* o = out + zo + sxyB;
+#pragma unroll
+                        for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
+                    }
+                }
+                if (storeA) {
                     sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
                     sum_phi += Io<S>::round_trip(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
                 if (storeB) {
-                    S* o = out + zo + sxyB;
-#pragma unroll
-                    for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
                     sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
                     sum_phi += Io<S>::round_trip(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
@@ -347,106 +580,23 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
             }
         }
 
-        float2 nYZ[9];
-        float nPA[9], nMB[9];
-        float2 n_hx, n_vzp, n_vzm;
-        float n_dyA, n_dyB;
-        // (d) plane i: stencils, collision, x sweep, y populations -> yx[i], S
-        {
-            const float* m = mom + ((i + 8) & 1) * 10 * NS + sA;
-            auto ld2 = [&](int f) { return make_float2(m[f * NS], m[f * NS + 32]); };
-            const float2 sgy = make_float2(sgyA, sgyB);
-            const float2 drho = ld2(0);
-            float2 ux = sgx * ld2(1), uy = sgy * ld2(2), uz = sgz_cur * ld2(3);
-            const float2 pxx = ld2(4), pyy = ld2(5), pzz = ld2(6);
-            const float2 pxy = (sgx * sgy) * ld2(7), pxz = (sgx * sgz_cur) * ld2(8), pyz = (sgz_cur * sgy) * ld2(9);
-            if (inl_cur) {
-                float ua[3], ub[3];
-                inlet_velocity(P, sx, syA, t, ua);
-                inlet_velocity(P, sx, syB, t, ub);
-                ux = make_float2(ua[0] * sgx, ub[0] * sgx);
-                uy = make_float2(ua[1] * sgyA, ub[1] * sgyB);
-                uz = make_float2(ua[2], ub[2]);
-            }
-
-            // interface terms from the z combinations of phi at plane i
-            float2 phi, Fx, Fy, Fz, nxv, nyv, nzv;
-            interface2<NPH>(zc + ((i + 8) & 1) * 3 * NPH, lane, w, sig_half, P.normal_eps2, phi, Fx, Fy, Fz,
-                            nxv, nyv, nzv);
-            if (inl_cur) {
-                Fx = Fy = Fz = bc(0.f);
-                nxv = nyv = nzv = bc(0.f);
-            }
-
-            // collision in Hermite form (Guo forcing: v = u + F / (2 rho))
-            const float2 rho = bc(1.f) + drho;
-            const float2 irho = rcp2(rho);
-            const float2 hf = 0.5f * irho;
-            const float2 hfx = hf * Fx, hfy = hf * Fy, hfz = hf * Fz;
-            const float2 vx = ux + hfx, vy = uy + hfy, vz = uz + hfz;
-            const float2 nxx = pxx - rho * mad(ux, hfx, hfx * vx);
-            const float2 nyy = pyy - rho * mad(uy, hfy, hfy * vy);
-            const float2 nzz = pzz - rho * mad(uz, hfz, hfz * vz);
-            const float2 nxy = pxy - rho * mad(ux, hfy, hfx * vy);
-            const float2 nxz = pxz - rho * mad(ux, hfz, hfx * vz);
-            const float2 nyz = pyz - rho * mad(uy, hfz, hfy * vz);
-            float2 X[3][8];
-            const float2 zero = bc(0.f);
-            collide_xsweep2(rho, drho, ux, uy, uz, vx, vy, vz, Fx, Fy, Fz, nxx, nyy, nzz, nxy, nxz, nyz, om1, fo, X);
-
-            // y populations; the row pair exchanges inside the thread, the pair
-            // edges go through shared memory: p(+1) of row 2w+1 to the thread
-            // below, p(-1) of row 2w to the thread above
-            float* yb = yx + ((i + 8) & 1) * 20 * NT + tid;
-#pragma unroll
-            for (int qx = 0; qx < 3; ++qx)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float2 b0 = X[qx][3 * c], b1 = X[qx][3 * c + 1];
-                    const float2 b2 = c < 2 ? X[qx][3 * c + 2] : zero;
-                    const Tri2 tr = pops2(b0, b1, b2);
-                    const int k = 3 * qx + c;
-                    yb[(2 * k) * NT] = tr.p.y;
-                    yb[(2 * k + 1) * NT] = tr.m.x;
-                    nYZ[k] = tr.z;
-                    nPA[k] = tr.p.x;
-                    nMB[k] = tr.m.y;
-                }
-
-            // D3Q7: g_i^post = w_i (B0 + c_i . B1)
-            const float2 ga = P.gamma * (bc(1.f) - phi * phi);
-            const float2 fphi = 4.f * phi;
-            const float2 b1x = mad(fphi, vx, ga * nxv);
-            const float2 b1y = mad(fphi, vy, ga * nyv);
-            const float2 b1z = mad(fphi, vz, ga * nzv);
-            const float2 fromL = shfl_up2(phi + b1x), fromR = shfl_down2(phi - b1x);
-            n_hx = mad(0.25f, phi, 0.125f * (fromL + fromR));
-            const float2 yp = phi + b1y, ym = phi - b1y;
-            yb[18 * NT] = yp.y;
-            yb[19 * NT] = ym.x;
-            n_dyA = ym.y;  // row 2w+1 -> row 2w
-            n_dyB = yp.x;  // row 2w -> row 2w+1
-            n_vzp = phi + b1z;
-            n_vzm = phi - b1z;
+        if (tst) fence_proxy_async();  // the staging box is read by the TMA store next iteration
+        if (i < z1) zcombine(i + 1);
+        commit(do_p, i + 2 + PF, do_m, i + PF);
+    }
+    // the last plane (z1 - 1) waits in its staging box
+    __syncthreads();
+    if (tst && tid == 0) {
+        if (!dead) {
+            tma_store_4d(&maps->out, outb + ((z1 - 1 + 8) & 1) * OSL, x0, y0, z1 - 1, 0);
+            bulk_commit();
         }
-        __syncthreads();
-        commit_phi(i + 3);
-        commit_mom(i + 1);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            sYZ[k] = nYZ[k];
-            sPA[k] = nPA[k];
-            sMB[k] = nMB[k];
-        }
-        s_hx = n_hx;
-        s_vzp = n_vzp;
-        s_vzm = n_vzm;
-        s_dyA = n_dyA;
-        s_dyB = n_dyB;
-        sgz_cur = sgz_nxt;
-        inl_cur = inl_nxt;
+        bulk_wait<0>();
     }
     cp_async_wait<0>();
+    // copies still in flight after a failed wait: give them a bounded chance to land
+    for (int k = 0; k < NB; ++k)
+        if ((pend >> k) & 1u) mbar_wait(bar + k, (phase >> k) & 1u);
 
     double a = sum_rho, b = sum_phi;
 #pragma unroll
@@ -476,12 +626,12 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const S* __restri
 // One time step of one grid: one block per tile.
 template <int NW, typename S>
 __global__ void __launch_bounds__(32 * NW, 1)
-    step2_kernel(const __grid_constant__ StepParams P, const S* __restrict__ in, S* __restrict__ out,
-                 const long long* __restrict__ t_in, long long* __restrict__ t_out,
+    step2_kernel(const __grid_constant__ StepParams P, const __grid_constant__ TileMaps M, const S* __restrict__ in,
+                 S* __restrict__ out, const long long* __restrict__ t_in, long long* __restrict__ t_out,
                  double* __restrict__ partials) {
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const long long t = *t_in;
-    step_tile<NW, S>(P, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+    step_tile<NW, S>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
     if (blk == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_out = t + 1;
 }
 
@@ -517,7 +667,8 @@ __global__ void __launch_bounds__(32 * NW, 1)
             }
         }
         __syncthreads();
-        step_tile<NW, float>(sP, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w, partials + 2 * k);
+        step_tile<NW, float>(sP, nullptr, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
+                             partials + 2 * k);
     }
     if (blockIdx.x == 0 && tid == 0) *t_out = t + 1;
 }
@@ -626,21 +777,26 @@ int conv_blocks(const StepParams& p) {
 }
 
 template <int NW, typename S>
-cudaError_t launch_nw(const StepParams& p, const void* in, void* out, const long long* t_in, long long* t_out,
-                      double* partials, cudaStream_t s) {
-    const LaunchShape sh = step_shape(p, ST_FP32);
-    step2_kernel<NW, S><<<sh.grid, sh.block, sh.smem, s>>>(p, static_cast<const S*>(in), static_cast<S*>(out),
-                                                           t_in, t_out, partials);
+cudaError_t launch_nw(const StepParams& p, int storage, const void* in, void* out, const long long* t_in,
+                      long long* t_out, double* partials, cudaStream_t s, const TileMaps* maps) {
+    const LaunchShape sh = step_shape(p, storage);
+    TileMaps none;
+    if (!maps) {
+        memset(&none, 0, sizeof(none));
+        maps = &none;
+    }
+    step2_kernel<NW, S><<<sh.grid, sh.block, sh.smem, s>>>(p, *maps, static_cast<const S*>(in),
+                                                           static_cast<S*>(out), t_in, t_out, partials);
     return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_step_t(const StepParams& p, const void* in, void* out, const long long* t_in,
-                          long long* t_out, double* partials, cudaStream_t s) {
+cudaError_t launch_step_t(const StepParams& p, int st, const void* in, void* out, const long long* t_in,
+                          long long* t_out, double* partials, cudaStream_t s, const TileMaps* m) {
     switch (p.block_warps) {
-        case 8: return launch_nw<8, S>(p, in, out, t_in, t_out, partials, s);
-        case 12: return launch_nw<12, S>(p, in, out, t_in, t_out, partials, s);
-        case 16: return launch_nw<16, S>(p, in, out, t_in, t_out, partials, s);
+        case 8: return launch_nw<8, S>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 12: return launch_nw<12, S>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 16: return launch_nw<16, S>(p, st, in, out, t_in, t_out, partials, s, m);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -648,15 +804,15 @@ cudaError_t launch_step_t(const StepParams& p, const void* in, void* out, const 
 template <int NW, typename S>
 cudaError_t prepare_nw() {
     return cudaFuncSetAttribute(step2_kernel<NW, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Step2Smem<NW>::BYTES);
+                                (int)Step2Smem<NW, S>::BYTES);
 }
 
 template <int NW>
 cudaError_t launch_batch_nw(const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
-                            const long long* t_in, long long* t_out, int* counters, double* partials, int nblocks,
+                            const long long* t_in, long long* t_out, int* counters, double* partials, int sms,
                             cudaStream_t s) {
-    step_batch_kernel<NW><<<nblocks, dim3(32, NW, 1), Step2Smem<NW>::BYTES, s>>>(insts, tiles, ntiles, parity, t_in,
-                                                                                  t_out, counters, partials);
+    step_batch_kernel<NW><<<sms, dim3(32, NW, 1), Step2Smem<NW, float>::BYTES, s>>>(
+        insts, tiles, ntiles, parity, t_in, t_out, counters, partials);
     return cudaGetLastError();
 }
 
@@ -668,25 +824,28 @@ cudaError_t prepare_t() {
     return e;
 }
 
+template <int NW>
+cudaError_t prepare_batch_nw() {
+    return cudaFuncSetAttribute(step_batch_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Step2Smem<NW, float>::BYTES);
+}
+
 }  // namespace
 
 static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied as ints");
 
 cudaError_t prepare_batch_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(step_batch_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Step2Smem<8>::BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step_batch_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Step2Smem<12>::BYTES);
+    cudaError_t e = prepare_batch_nw<8>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12>();
     return e;
 }
 
 cudaError_t launch_batch_step(int nw, const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
                               const long long* t_in, long long* t_out, int* counters, double* partials,
-                              int nblocks, cudaStream_t s) {
+                              int sms, cudaStream_t s) {
     switch (nw) {
-        case 8: return launch_batch_nw<8>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, nblocks, s);
-        case 12: return launch_batch_nw<12>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, nblocks, s);
+        case 8: return launch_batch_nw<8>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
+        case 12: return launch_batch_nw<12>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -700,21 +859,31 @@ cudaError_t prepare_kernels(int storage) {
     }
 }
 
-size_t step_smem_bytes(int nw) {
+template <typename S>
+size_t step_smem_bytes_t(int nw) {
     switch (nw) {
-        case 8: return Step2Smem<8>::BYTES;
-        case 12: return Step2Smem<12>::BYTES;
-        default: return Step2Smem<16>::BYTES;
+        case 8: return Step2Smem<8, S>::BYTES;
+        case 12: return Step2Smem<12, S>::BYTES;
+        default: return Step2Smem<16, S>::BYTES;
     }
 }
 
-LaunchShape step_shape(const StepParams& p, int /*storage*/) {
+size_t step_smem_bytes(int nw, int storage) {
+    return storage == ST_FP32 ? step_smem_bytes_t<float>(nw) : step_smem_bytes_t<__half>(nw);
+}
+
+LaunchShape step_shape(const StepParams& p, int storage) {
     LaunchShape sh;
     sh.nw = p.block_warps;
     const int ty = 2 * sh.nw - 2;
-    sh.grid = dim3((p.nx + TX - 1) / TX, (p.ny + ty - 1) / ty, (p.nz + p.tile_z - 1) / p.tile_z);
+    // tile width: the projection step's FP32 tiles are 16-byte aligned (28), the
+    // rest (16-bit storage, the Chapman-Enskog step) 30 columns
+    const int tx = p.closure == CL_CHAPMAN_ENSKOG ? TX
+                   : storage == ST_FP32           ? Step2Smem<8, float>::TXS
+                                                  : Step2Smem<8, __half>::TXS;
+    sh.grid = dim3((p.nx + tx - 1) / tx, (p.ny + ty - 1) / ty, (p.nz + p.tile_z - 1) / p.tile_z);
     sh.block = dim3(32, sh.nw, 1);
-    sh.smem = step_smem_bytes(sh.nw);
+    sh.smem = step_smem_bytes(sh.nw, storage);
     return sh;
 }
 
@@ -729,13 +898,78 @@ int max_partials(const StepParams& p, int storage) {
 }
 
 cudaError_t launch_step(const StepParams& p, int storage, const void* in, void* out, const long long* t_in,
-                        long long* t_out, double* partials, cudaStream_t s) {
+                        long long* t_out, double* partials, cudaStream_t s, const TileMaps* maps) {
     switch (storage) {
-        case ST_FP32: return launch_step_t<float>(p, in, out, t_in, t_out, partials, s);
-        case ST_FP16: return launch_step_t<__half>(p, in, out, t_in, t_out, partials, s);
-        case ST_BF16: return launch_step_t<__nv_bfloat16>(p, in, out, t_in, t_out, partials, s);
+        case ST_FP32: return launch_step_t<float>(p, storage, in, out, t_in, t_out, partials, s, maps);
+        case ST_FP16: return launch_step_t<__half>(p, storage, in, out, t_in, t_out, partials, s, maps);
+        case ST_BF16: return launch_step_t<__nv_bfloat16>(p, storage, in, out, t_in, t_out, partials, s, maps);
         default: return cudaErrorInvalidValue;
     }
+}
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled of the driver, looked up through the runtime (the
+// library does not link libcuda directly); null if unavailable.
+EncodeTiled encode_tiled() {
+    static EncodeTiled fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiled>(f);
+    }();
+    return fn;
+}
+
+template <typename S>
+cudaError_t make_maps_t(const StepParams& p, const void* buf, const void* obuf, TileMaps* m) {
+    const int nw = p.block_warps;
+    const int nr = 2 * nw;
+    const int mw = Step2Smem<8, S>::MW, pw = Step2Smem<8, S>::PW, txs = Step2Smem<8, S>::TXS;
+    const cuuint64_t es = sizeof(S);
+    const CUtensorMapDataType dt = sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return cudaSuccess;  // valid stays 0: element-wise loads
+    const cuuint64_t dm[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz, 10};
+    const cuuint64_t sm[3] = {p.nx * es, (cuuint64_t)p.nx * p.ny * es, (cuuint64_t)p.fstride * es};
+    const cuuint32_t bm[4] = {(cuuint32_t)mw, (cuuint32_t)nr, 1, 10};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    CUresult r = enc(&m->mom, dt, 4, const_cast<void*>(buf), dm, sm, bm, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaSuccess;
+    const cuuint32_t bp[3] = {(cuuint32_t)pw, (cuuint32_t)(nr + 2), 1};
+    const void* pbase = static_cast<const char*>(buf) + (size_t)F_PHI * p.fstride * es;
+    r = enc(&m->phi, dt, 3, const_cast<void*>(pbase), dm, sm, bp, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaSuccess;
+    m->valid = 1;
+    m->block_warps = nw;
+    if (Step2Smem<8, S>::kFp32 && obuf && reinterpret_cast<uintptr_t>(obuf) % 16 == 0) {
+        const cuuint64_t dout[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz, (cuuint64_t)NFIELDS};
+        const cuuint32_t bo[4] = {(cuuint32_t)txs, (cuuint32_t)(nr - 2), 1, (cuuint32_t)NFIELDS};
+        r = enc(&m->out, dt, 4, const_cast<void*>(obuf), dout, sm, bo, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS) m->store = 1;
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t make_tile_maps(const StepParams& p, int storage, const void* buf, const void* obuf, TileMaps* maps) {
+    memset(maps, 0, sizeof(*maps));
+    const size_t es = storage == ST_FP32 ? 4 : 2;
+    // TMA needs 16-byte aligned row pitches and bases; box sizes exist for 8, 12 and 16 warps
+    if (p.closure != CL_PROJECTION || ((size_t)p.nx * es) % 16 != 0 ||
+        (reinterpret_cast<uintptr_t>(buf) % 16) != 0 ||
+        (p.block_warps != 8 && p.block_warps != 12 && p.block_warps != 16))
+        return cudaSuccess;
+    return storage == ST_FP32 ? make_maps_t<float>(p, buf, obuf, maps) : make_maps_t<__half>(p, buf, obuf, maps);
 }
 
 cudaError_t launch_put_field(const StepParams& p, int storage, const float* src, int field, void* state,
