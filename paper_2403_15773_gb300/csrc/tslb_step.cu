@@ -91,8 +91,12 @@ struct Step2Smem {
     static_assert(BYTES <= 227 * 1024, "more shared memory than a block can have");
 };
 
+// The dynamic shared memory base rounded up to 128 bytes (TMA boxes).  The
+// offset is added to the shared array itself so that the compiler keeps
+// addressing it as shared memory (a round trip through an integer address
+// would turn every access into a generic load or store).
 __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
-    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
+    return p + ((0u - smem_u32(p)) & 127u);
 }
 
 // One tile of one time step: the 30 x (2 NW - 2) interior columns at tile
