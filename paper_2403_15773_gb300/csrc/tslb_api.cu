@@ -841,6 +841,28 @@ tslb_status tslb_get_time(const tslb_ctx* c, int64_t* t) {
     return TSLB_OK;
 }
 
+// Slab depths tried for blocks of nw warps: the fixed list, plus (one grid)
+// the depths that fill k = 2 .. 8 waves of one block per SM to at least 90 %
+// (a last, partly empty wave costs as much as a full one).
+std::vector<int> slab_candidates(const tslb_ctx* c, int nw) {
+    std::vector<int> tz(std::begin(kAutotuneTileZ), std::end(kAutotuneTileZ));
+    if (!c->batch) {
+        const StepParams& p = c->inst[0].p;
+        const long long txy = tiles_of(p, c->storage, nw, p.nz);  // tiles of one full-depth slab
+        for (int k = 2; k <= 8; ++k) {
+            const long long slabs = (long long)k * c->sms / txy;
+            if (slabs < 1) continue;
+            const int d = (int)((p.nz + slabs - 1) / slabs);
+            const long long blocks = txy * ((p.nz + d - 1) / d);
+            if (d >= 8 && d <= p.nz && blocks * 10 >= (long long)k * c->sms * 9 && blocks <= (long long)k * c->sms)
+                tz.push_back(d);
+        }
+    }
+    std::sort(tz.begin(), tz.end());
+    tz.erase(std::unique(tz.begin(), tz.end()), tz.end());
+    return tz;
+}
+
 tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z) {
     if (!c) return TSLB_ERR_INVALID_ARG;
     if (steps_per_trial < 1) return bad(c, "steps_per_trial must be >= 1");
@@ -864,7 +886,7 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     int best_tz = keep_tz[0];
     tslb_status st = TSLB_OK;
     for (size_t si = 0; si < shapes.size() && st == TSLB_OK; ++si)
-        for (int tz : kAutotuneTileZ) {
+        for (int tz : slab_candidates(c, shapes[si])) {
             // each trial re-runs the step from the current state into the other
             // buffer, so the state itself does not advance
             for (Instance& I : c->inst) {

@@ -79,8 +79,9 @@ struct Step2Smem {
     static constexpr int MS = PF + 1, PS = PF + 3, NB = PF + 2;      // moment slots, phase slots, mbarriers
     static constexpr size_t MOM = 0;                                 // [MS] moment boxes
     static constexpr size_t RING = MOM + MS * MOM_SLOT;              // [PS] phase-field boxes
-    static constexpr size_t ZC = RING + PS * PHI_SLOT;               // [NPH] float4 z combinations
-    static constexpr size_t YX = ZC + 16 * (size_t)NPH;              // [20][NT] float y exchange
+    static constexpr int EPT = (NPH + NT - 1) / NT;                  // phase-field elements per thread
+    static constexpr size_t ZC = RING + PS * PHI_SLOT;               // [EPT * NT] float4 z combinations
+    static constexpr size_t YX = ZC + 16 * (size_t)EPT * NT;         // [20][NT] float y exchange
     static constexpr size_t OUT_BOX = kTmaStore ? sizeof(float) * NFIELDS * TY * TXS : 0;  // [11][TY][TXS]
     static constexpr size_t OUT_SLOT = r128(OUT_BOX);
     static constexpr size_t OUT = r128(YX + sizeof(float) * 20 * NT);  // [2] output staging boxes
@@ -111,7 +112,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     constexpr int NT = L::NT, NR = L::NR, NPH = L::NPH, MW = L::MW, PW = L::PW, FS = L::FS, AL = L::AL;
     constexpr int TY = L::TY, TX = L::TXS;
     constexpr int OSL = (int)(L::OUT_SLOT / sizeof(float));
-    constexpr int EPT = (NPH + NT - 1) / NT;
+    constexpr int EPT = L::EPT;
     constexpr int MSL = (int)(L::MOM_SLOT / sizeof(S)), PSL = (int)(L::PHI_SLOT / sizeof(S));
     constexpr int PF = L::PF, MS = L::MS, PS = L::PS, NB = L::NB;
     // slots of plane q (q >= -2) and the mbarrier of the loads issued at iteration i (>= -1)
@@ -295,16 +296,14 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         const S* pp = ring + pslot(q + 1) * PSL;
         const bool im = inlet_face && q - 1 < 0, ic = inlet_face && q < 0;
         const float inv = P.inv_scale[F_PHI];
+        // (elements beyond NPH read box position 0 and fill padding of zc)
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-            const int idx = tid + e * NT;
-            if (idx < NPH) {
-                const float a = im ? phib[e] : Io<S>::cvt(pm[prd[e]], inv);
-                const float b = ic ? phib[e] : Io<S>::cvt(pc[prd[e]], inv);
-                const float c = Io<S>::cvt(pp[prd[e]], inv);
-                const float s = c + a;
-                zc[idx] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
-            }
+            const float a = im ? phib[e] : Io<S>::cvt(pm[prd[e]], inv);
+            const float b = ic ? phib[e] : Io<S>::cvt(pc[prd[e]], inv);
+            const float c = Io<S>::cvt(pp[prd[e]], inv);
+            const float s = c + a;
+            zc[tid + e * NT] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
         }
     };
 
@@ -520,7 +519,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
             cVPP = cVP;
             cVP = h_vzp;
 
-            if (i >= z0 + 1 && (storeA || storeB)) {
+            if (i >= z0 + 1) {  // (every lane computes; halo and out-of-grid lanes do not write)
                 const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
                 const float2 rn = bc(1.f) + dr, irn = rcp2(rn);
                 const float2 ux = jx * irn, uy = jy * irn, uz = jz * irn;
