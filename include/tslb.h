@@ -52,7 +52,8 @@ typedef enum {
     TSLB_ERR_OOM = 2,         /* device or host allocation failed / workspace too small */
     TSLB_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
     TSLB_ERR_UNSTABLE = 4,    /* the total mass or phase field became non-finite */
-    TSLB_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    TSLB_ERR_TIMEOUT = 5,     /* a step kernel's bounded wait for its tile data gave up (reported by
+                                 tslb_sums and the check_every checks) */
     TSLB_ERR_STATE = 6        /* call out of order (e.g. tslb_step before tslb_set_state) */
 } tslb_status;
 
@@ -113,8 +114,9 @@ typedef struct {
                                for grids too small to fill the GPU) */
     int32_t graph_steps;    /* steps per captured CUDA graph replayed by tslb_step; 0 = automatic,
                                1 = plain launches */
-    int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 30 x 14,
-                               30 x 22, 30 x 30 interior nodes); 0 = 8 */
+    int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 14, 22 or
+                               30 interior rows; 28 interior columns with FP32 storage, 30 with
+                               16-bit storage or the Chapman-Enskog closure); 0 = 8 */
     int32_t scheme;         /* 0: the fused moment-only step (default, 88 B per update in FP32);
                                1: the paper's two-sweep design kept as an ablation: collide+push
                                into 34 population arrays in HBM, then their moments (360 B per
@@ -233,9 +235,11 @@ TSLB_API tslb_status tslb_get_averages(tslb_ctx* ctx, int32_t instance, double* 
 TSLB_API tslb_status tslb_reset_averages(tslb_ctx* ctx);
 
 /* Tile-shape autotuner: times the step kernel for blocks of 8 and 12 warps
- * and z slabs of 16, 24, 32, 48 and 64 planes (steps_per_trial launches
- * each, CUDA events on the context stream) and keeps the fastest for all
- * later steps.  Every trial recomputes the step from the current state into
+ * (and 16 for one grid under the projection closure) and z slabs of 16, 24,
+ * 32, 48 and 64 planes, plus, for one grid, the slab depths whose block count
+ * fills 2 to 8 waves of one block per SM to at least 90 % (steps_per_trial
+ * launches each, CUDA events on the context stream), and keeps the fastest
+ * for all later steps.  Every trial recomputes the step from the current state into
  * the spare buffer, so the state and the step index do not change.  Drops
  * captured graphs; synchronises.  Reports the choice in *block_warps and
  * *tile_z (either may be NULL). */
