@@ -247,12 +247,31 @@ __device__ __forceinline__ Tri2 pops2(float2 k0, float2 k1, float2 k2) {
     const float2 s = k0 + k2;
     return {s - k1, mad(4.f, k0, -2.f * k2), s + k1};
 }
-// x sweep of two nodes: shifts along the warp (lanes = x), then x moments.
+// ... for k2 = 0
+__device__ __forceinline__ Tri2 pops2_01(float2 k0, float2 k1) { return {k0 - k1, 4.f * k0, k0 + k1}; }
+// x sweep of two nodes: shifts along the warp (lanes = x), then x moments;
+// the rest population 4 k0 - 2 k2 is folded into M0 (it is not shifted).
 __device__ __forceinline__ void xsweep2(float2 k0, float2 k1, float2 k2, float2& m0, float2& m1, float2& m2) {
-    const Tri2 t = pops2(k0, k1, k2);
-    const float2 qp = shfl_up2(t.p), qm = shfl_down2(t.m);
+    const float2 s0 = k0 + k2;
+    const float2 qp = shfl_up2(s0 + k1), qm = shfl_down2(s0 - k1);
     const float2 s = qp + qm;
-    m0 = s + t.z;
+    m0 = mad(4.f, k0, mad(-2.f, k2, s));
+    m1 = qp - qm;
+    m2 = s;
+}
+// ... for k2 = 0
+__device__ __forceinline__ void xsweep2_01(float2 k0, float2 k1, float2& m0, float2& m1, float2& m2) {
+    const float2 qp = shfl_up2(k0 + k1), qm = shfl_down2(k0 - k1);
+    const float2 s = qp + qm;
+    m0 = mad(4.f, k0, s);
+    m1 = qp - qm;
+    m2 = s;
+}
+// ... for k1 = k2 = 0
+__device__ __forceinline__ void xsweep2_0(float2 k0, float2& m0, float2& m1, float2& m2) {
+    const float2 qp = shfl_up2(k0), qm = shfl_down2(k0);
+    const float2 s = qp + qm;
+    m0 = mad(4.f, k0, s);
     m1 = qp - qm;
     m2 = s;
 }
@@ -385,10 +404,13 @@ __device__ __forceinline__ void interface4(const float4* zb, int lane, int w, fl
 // (Eq. fullstrcoll, eqts, noneqts with Guo forcing, v = u + F/(2 rho)), where
 // N is the non-equilibrium second moment relative to rho v v; then streams
 // them along x (warp shuffles) into X[x moment][3 c + b] (y index b, z index c).
+// The forcing products come from the caller: fvaa = F_a v_a (diagonal) and
+// gab = v_a F_b + F_a v_b (off-diagonal).
 __device__ __forceinline__ void collide_xsweep2(float2 rho, float2 drho, float2 ux, float2 uy, float2 uz, float2 vx,
                                                 float2 vy, float2 vz, float2 Fx, float2 Fy, float2 Fz, float2 nxx,
                                                 float2 nyy, float2 nzz, float2 nxy, float2 nxz, float2 nyz,
-                                                float om1, float fo, float2 (&X)[3][8]) {
+                                                float2 fvxx, float2 fvyy, float2 fvzz, float2 gxy, float2 gxz,
+                                                float2 gyz, float om1, float fo, float2 (&X)[3][8]) {
     const float2 rvx = rho * vx, rvy = rho * vy, rvz = rho * vz;
     const float2 exx = rvx * vx, eyy = rvy * vy, ezz = rvz * vz;
     const float2 exy = rvx * vy, exz = rvx * vz, eyz = rvy * vz;
@@ -398,12 +420,12 @@ __device__ __forceinline__ void collide_xsweep2(float2 rho, float2 drho, float2 
     const float2 Mxx = mad(third, exx, qxx), Myy = mad(third, eyy, qyy), Mzz = mad(third, ezz, qzz);
     const float2 Mxy = mad(third, exy, qxy), Mxz = mad(third, exz, qxz), Myz = mad(third, eyz, qyz);
     const float2 f2o = bc(2.f * fo), f1o = bc(fo);
-    const float2 A2xx = mad(f2o, vx * Fx, exx + qxx);
-    const float2 A2yy = mad(f2o, vy * Fy, eyy + qyy);
-    const float2 A2zz = mad(f2o, vz * Fz, ezz + qzz);
-    const float2 A2xy = mad(f1o, mad(vx, Fy, Fx * vy), exy + qxy);
-    const float2 A2xz = mad(f1o, mad(vx, Fz, Fx * vz), exz + qxz);
-    const float2 A2yz = mad(f1o, mad(vy, Fz, Fy * vz), eyz + qyz);
+    const float2 A2xx = mad(f2o, fvxx, exx + qxx);
+    const float2 A2yy = mad(f2o, fvyy, eyy + qyy);
+    const float2 A2zz = mad(f2o, fvzz, ezz + qzz);
+    const float2 A2xy = mad(f1o, gxy, exy + qxy);
+    const float2 A2xz = mad(f1o, gxz, exz + qxz);
+    const float2 A2yz = mad(f1o, gyz, eyz + qyz);
 
     // tensor-product Hermite coefficients k_abc, index 2 pre-multiplied by
     // 2/3, everything pre-divided by 216 (the 6^3 of the unnormalised sweeps)
@@ -421,15 +443,14 @@ __device__ __forceinline__ void collide_xsweep2(float2 rho, float2 drho, float2 
     const float2 k012 = c24 * mad(tz, Myz, vy * Mzz);
     const float2 k111 = (1.f / 8.f) * mad(vx, Myz, mad(vy, Mxz, vz * Mxy));
 
-    const float2 zero = bc(0.f);
     xsweep2(k000, k100, k200, X[0][0], X[1][0], X[2][0]);
     xsweep2(k010, k110, k210, X[0][1], X[1][1], X[2][1]);
-    xsweep2(k020, k120, zero, X[0][2], X[1][2], X[2][2]);
+    xsweep2_01(k020, k120, X[0][2], X[1][2], X[2][2]);
     xsweep2(k001, k101, k201, X[0][3], X[1][3], X[2][3]);
-    xsweep2(k011, k111, zero, X[0][4], X[1][4], X[2][4]);
-    xsweep2(k021, zero, zero, X[0][5], X[1][5], X[2][5]);
-    xsweep2(k002, k102, zero, X[0][6], X[1][6], X[2][6]);
-    xsweep2(k012, zero, zero, X[0][7], X[1][7], X[2][7]);
+    xsweep2_01(k011, k111, X[0][4], X[1][4], X[2][4]);
+    xsweep2_0(k021, X[0][5], X[1][5], X[2][5]);
+    xsweep2_01(k002, k102, X[0][6], X[1][6], X[2][6]);
+    xsweep2_0(k012, X[0][7], X[1][7], X[2][7]);
 }
 
 }  // namespace

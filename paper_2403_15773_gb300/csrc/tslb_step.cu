@@ -427,8 +427,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
             const float2 rho = bc(1.f) + drho;
             const float2 irho = rcp2(rho);
             const float2 hf = 0.5f * irho;
-            const float2 hfx = hf * Fx, hfy = hf * Fy, hfz = hf * Fz;
-            const float2 vx = ux + hfx, vy = uy + hfy, vz = uz + hfz;
+            const float2 vx = mad(hf, Fx, ux), vy = mad(hf, Fy, uy), vz = mad(hf, Fz, uz);
 
             // D3Q7: g_i^post = w_i (B0 + c_i . B1); x terms by shuffles, the
             // y terms of the row pair's edges through shared memory
@@ -450,16 +449,21 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
                 h_vzm = phi - b1z;
             }
 
-            // collision in Hermite form
-            const float2 nxx = pxx - rho * mad(ux, hfx, hfx * vx);
-            const float2 nyy = pyy - rho * mad(uy, hfy, hfy * vy);
-            const float2 nzz = pzz - rho * mad(uz, hfz, hfz * vz);
-            const float2 nxy = pxy - rho * mad(ux, hfy, hfx * vy);
-            const float2 nxz = pxz - rho * mad(ux, hfz, hfx * vz);
-            const float2 nyz = pyz - rho * mad(uy, hfz, hfy * vz);
+            // collision in Hermite form.  Non-equilibrium second moment relative
+            // to rho v v: N = P + rho u u - rho v v = P - (u F + F v) / 2
+            // (rho (v - u) = F / 2); forcing products F_a v_b shared with
+            // the (1 - omega/2)(v F + F v) term.
+            const float2 fvxx = Fx * vx, fvyy = Fy * vy, fvzz = Fz * vz;
+            const float2 fxvy = Fx * vy, fxvz = Fx * vz, fyvz = Fy * vz;
+            const float2 nxx = mad(-0.5f, mad(Fx, ux, fvxx), pxx);
+            const float2 nyy = mad(-0.5f, mad(Fy, uy, fvyy), pyy);
+            const float2 nzz = mad(-0.5f, mad(Fz, uz, fvzz), pzz);
+            const float2 nxy = mad(-0.5f, mad(ux, Fy, fxvy), pxy);
+            const float2 nxz = mad(-0.5f, mad(ux, Fz, fxvz), pxz);
+            const float2 nyz = mad(-0.5f, mad(uy, Fz, fyvz), pyz);
             float2 X[3][8];
-            const float2 zero = bc(0.f);
-            collide_xsweep2(rho, drho, ux, uy, uz, vx, vy, vz, Fx, Fy, Fz, nxx, nyy, nzz, nxy, nxz, nyz, om1, fo, X);
+            collide_xsweep2(rho, drho, ux, uy, uz, vx, vy, vz, Fx, Fy, Fz, nxx, nyy, nzz, nxy, nxz, nyz, fvxx, fvyy,
+                            fvzz, mad(vx, Fy, fxvy), mad(vx, Fz, fxvz), mad(vy, Fz, fyvz), om1, fo, X);
 
             // y populations; the row pair exchanges inside the thread, the pair
             // edges go through shared memory: p(+1) of row 2w+1 to the thread
@@ -469,8 +473,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
 #pragma unroll
                 for (int qx = 0; qx < 3; ++qx) {
                     const float2 b0 = X[qx][3 * c], b1 = X[qx][3 * c + 1];
-                    const float2 b2 = c < 2 ? X[qx][3 * c + 2] : zero;
-                    const Tri2 tr = pops2(b0, b1, b2);
+                    const Tri2 tr = c < 2 ? pops2(b0, b1, X[qx][3 * c + 2]) : pops2_01(b0, b1);
                     const int k = 3 * qx + c;
                     yb[(2 * k) * NT] = tr.p.y;
                     yb[(2 * k + 1) * NT] = tr.m.x;

@@ -415,7 +415,9 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
             const float2 hf = 0.5f * irho;
             const float2 vx = mad(hf, Fx, ux), vy = mad(hf, Fy, uy), vz = mad(hf, Fz, uz);
             float2 X[3][8];
-            collide_xsweep2(rho, drho, ux, uy, uz, vx, vy, vz, Fx, Fy, Fz, nxx, nyy, nzz, nxy, nxz, nyz, om1, fo, X);
+            collide_xsweep2(rho, drho, ux, uy, uz, vx, vy, vz, Fx, Fy, Fz, nxx, nyy, nzz, nxy, nxz, nyz, vx * Fx,
+                            vy * Fy, vz * Fz, mad(vx, Fy, Fx * vy), mad(vx, Fz, Fx * vz), mad(vy, Fz, Fy * vz), om1,
+                            fo, X);
 
             // y populations of the x moments 0 and 1; the row pair exchanges
             // inside the thread, the pair edges go through shared memory
