@@ -414,34 +414,33 @@ __device__ __forceinline__ void collide_xsweep2(float2 rho, float2 drho, float2 
     const float2 rvx = rho * vx, rvy = rho * vy, rvz = rho * vz;
     const float2 exx = rvx * vx, eyy = rvy * vy, ezz = rvz * vz;
     const float2 exy = rvx * vy, exz = rvx * vz, eyz = rvy * vz;
-    const float2 o1 = bc(om1), third = bc(1.f / 3.f);
-    const float2 qxx = o1 * nxx, qyy = o1 * nyy, qzz = o1 * nzz;
-    const float2 qxy = o1 * nxy, qxz = o1 * nxz, qyz = o1 * nyz;
-    const float2 Mxx = mad(third, exx, qxx), Myy = mad(third, eyy, qyy), Mzz = mad(third, ezz, qzz);
-    const float2 Mxy = mad(third, exy, qxy), Mxz = mad(third, exz, qxz), Myz = mad(third, eyz, qyz);
-    const float2 f2o = bc(2.f * fo), f1o = bc(fo);
-    const float2 A2xx = mad(f2o, fvxx, exx + qxx);
-    const float2 A2yy = mad(f2o, fvyy, eyy + qyy);
-    const float2 A2zz = mad(f2o, fvzz, ezz + qzz);
-    const float2 A2xy = mad(f1o, gxy, exy + qxy);
-    const float2 A2xz = mad(f1o, gxz, exz + qxz);
-    const float2 A2yz = mad(f1o, gyz, eyz + qyz);
+    // q = (1 - omega) N and M = rho v v / 3 + q enter pre-divided by 24
+    const float2 o24 = bc(om1 * (1.f / 24.f)), c72 = bc(1.f / 72.f), c24 = bc(1.f / 24.f);
+    const float2 qxx = o24 * nxx, qyy = o24 * nyy, qzz = o24 * nzz;
+    const float2 qxy = o24 * nxy, qxz = o24 * nxz, qyz = o24 * nyz;
+    const float2 Mxx = mad(c72, exx, qxx), Myy = mad(c72, eyy, qyy), Mzz = mad(c72, ezz, qzz);
+    const float2 Mxy = mad(c72, exy, qxy), Mxz = mad(c72, exz, qxz), Myz = mad(c72, eyz, qyz);
 
     // tensor-product Hermite coefficients k_abc, index 2 pre-multiplied by
-    // 2/3, everything pre-divided by 216 (the 6^3 of the unnormalised sweeps)
-    const float2 c72 = bc(1.f / 72.f), c24 = bc(1.f / 24.f);
+    // 2/3, everything pre-divided by 216 (the 6^3 of the unnormalised sweeps):
+    // k200 = A2xx / 72, k110 = A2xy / 24 with A2 = e + 24 q + (1 - omega/2) G
+    const float2 f72 = bc(2.f * fo * (1.f / 72.f)), f24 = bc(fo * (1.f / 24.f)), third = bc(1.f / 3.f);
     const float2 k000 = (1.f / 216.f) * drho;
     const float2 k100 = c72 * mad(rho, ux, Fx), k010 = c72 * mad(rho, uy, Fy), k001 = c72 * mad(rho, uz, Fz);
-    const float2 k200 = c72 * A2xx, k020 = c72 * A2yy, k002 = c72 * A2zz;
-    const float2 k110 = c24 * A2xy, k101 = c24 * A2xz, k011 = c24 * A2yz;
+    const float2 k200 = mad(c72, exx, mad(third, qxx, f72 * fvxx));
+    const float2 k020 = mad(c72, eyy, mad(third, qyy, f72 * fvyy));
+    const float2 k002 = mad(c72, ezz, mad(third, qzz, f72 * fvzz));
+    const float2 k110 = mad(c24, exy, mad(f24, gxy, qxy));
+    const float2 k101 = mad(c24, exz, mad(f24, gxz, qxz));
+    const float2 k011 = mad(c24, eyz, mad(f24, gyz, qyz));
     const float2 tx = 2.f * vx, ty = 2.f * vy, tz = 2.f * vz;
-    const float2 k210 = c24 * mad(tx, Mxy, vy * Mxx);
-    const float2 k201 = c24 * mad(tx, Mxz, vz * Mxx);
-    const float2 k120 = c24 * mad(ty, Mxy, vx * Myy);
-    const float2 k021 = c24 * mad(ty, Myz, vz * Myy);
-    const float2 k102 = c24 * mad(tz, Mxz, vx * Mzz);
-    const float2 k012 = c24 * mad(tz, Myz, vy * Mzz);
-    const float2 k111 = (1.f / 8.f) * mad(vx, Myz, mad(vy, Mxz, vz * Mxy));
+    const float2 k210 = mad(tx, Mxy, vy * Mxx);
+    const float2 k201 = mad(tx, Mxz, vz * Mxx);
+    const float2 k120 = mad(ty, Mxy, vx * Myy);
+    const float2 k021 = mad(ty, Myz, vz * Myy);
+    const float2 k102 = mad(tz, Mxz, vx * Mzz);
+    const float2 k012 = mad(tz, Myz, vy * Mzz);
+    const float2 k111 = 3.f * mad(vx, Myz, mad(vy, Mxz, vz * Mxy));
 
     xsweep2(k000, k100, k200, X[0][0], X[1][0], X[2][0]);
     xsweep2(k010, k110, k210, X[0][1], X[1][1], X[2][1]);

@@ -353,10 +353,15 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     __syncthreads();
     zcombine(z0 - 1);
 
-    float2 cPP[6], cP[6], cZ[6];
+    // z march carries: for the groups whose z moments 1, 2 are needed
+    // (g < 3) p(i-2), z(i-1) and p(i-1); for the others (and phi) the partial
+    // zeroth moment p(i-2) + z(i-1) and p(i-1)
+    float2 cPP[3], cZ[3], cP[6], cA[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) cPP[k] = cP[k] = cZ[k] = bc(0.f);
-    float2 cH = bc(0.f), cVPP = bc(0.f), cVP = bc(0.f);
+    for (int k = 0; k < 6; ++k) cP[k] = cA[k] = bc(0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cPP[k] = cZ[k] = bc(0.f);
+    float2 cAph = bc(0.f), cVP = bc(0.f);
     float sum_rho = 0.f, sum_phi = 0.f;
 
     const float om1 = 1.f - P.omega, fo = 1.f - 0.5f * P.omega;
@@ -510,16 +515,20 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
 #pragma unroll
             for (int g = 0; g < 6; ++g) {
                 const Tri2 tr = pops2(Y[gqx[g]][gqy[g]][0], Y[gqx[g]][gqy[g]][1], Y[gqx[g]][gqy[g]][2]);
-                O0[g] = cPP[g] + cZ[g] + tr.m;
-                O1[g] = cPP[g] - tr.m;
-                O2[g] = cPP[g] + tr.m;
-                cPP[g] = cP[g];
+                if (g < 3) {
+                    O0[g] = cPP[g] + cZ[g] + tr.m;
+                    O1[g] = cPP[g] - tr.m;
+                    O2[g] = cPP[g] + tr.m;
+                    cPP[g] = cP[g];
+                    cZ[g] = tr.z;
+                } else {
+                    O0[g] = cA[g] + tr.m;
+                    cA[g] = cP[g] + tr.z;
+                }
                 cP[g] = tr.p;
-                cZ[g] = tr.z;
             }
-            const float2 phin = mad(0.125f, cVPP + h_vzm, cH);
-            cH = hxy;
-            cVPP = cVP;
+            const float2 phin = mad(0.125f, h_vzm, cAph);
+            cAph = mad(0.125f, cVP, hxy);
             cVP = h_vzp;
 
             if (i >= z0 + 1) {  // (every lane computes; halo and out-of-grid lanes do not write)
