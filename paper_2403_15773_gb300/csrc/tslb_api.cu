@@ -339,6 +339,8 @@ tslb_status upload_batch(tslb_ctx* c) {
         di[i].p = I.p;
         di[i].buf[0] = I.buf[0];
         di[i].buf[1] = I.buf[1];
+        for (int q = 0; q < 2; ++q)
+            CK(tslb::make_tile_maps(I.p, c->storage, I.buf[q], I.buf[q ^ 1], &di[i].maps[q]), "batch tensor maps");
     }
     if ((int)tiles.size() > c->max_tiles) return bad(c, "batch tile list exceeds its workspace");
     c->ntiles = (int)tiles.size();

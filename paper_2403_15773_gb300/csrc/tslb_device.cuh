@@ -120,6 +120,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// Orders this thread's later TMA uses of the tensor maps at `m` (device
+// memory, written before the launch) after their generic-proxy contents.
+template <typename T>
+__device__ __forceinline__ void fence_tensormap_acquire(const T* m) {
+    constexpr int n = (int)(sizeof(T) / 128);
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(
+                         reinterpret_cast<const char*>(m) + 128 * k)
+                     : "memory");
+}
 // Bounded wait for the completion of phase `parity` of an mbarrier: gives up
 // (returns false) after about kWaitCycles SM cycles (~1 s) instead of spinning
 // forever if the copies it counts never arrive.

@@ -59,10 +59,14 @@ struct TileMaps {
     int block_warps;
 };
 
-// One grid of a batch: its parameters and its two state buffers.
+
+
+// One grid of a batch: its parameters, its two state buffers and the tensor
+// maps of the steps from buf[q] to buf[q ^ 1] (device memory, 64-byte aligned).
 struct BatchInstance {
     StepParams p;
     const void* buf[2];
+    TileMaps maps[2];
 };
 
 struct LaunchShape {

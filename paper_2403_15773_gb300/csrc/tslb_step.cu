@@ -601,6 +601,8 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     }
     // the last plane (z1 - 1) waits in its staging box
     __syncthreads();
+    if (use_maps && tid == 0)  // the next tile of a persistent block initialises them again
+        for (int k = 0; k < NB; ++k) mbar_inval(bar + k);
     if (tst && tid == 0) {
         if (!dead) {
             tma_store_4d(&maps->out, outb + ((z1 - 1 + 8) & 1) * OSL, x0, y0, z1 - 1, 0);
@@ -653,7 +655,8 @@ __global__ void __launch_bounds__(32 * NW, 1)
 // One time step of a batch of independent grids in one persistent launch:
 // each block takes the next tile of the batch's tile list from a device
 // counter (tiles[k] = instance, bx, by, bz) until the list is exhausted.  The
-// instance's parameters are staged in shared memory for the tile.  counters[q]
+// instance's parameters are staged in shared memory for the tile; its tensor
+// maps are read from the instance table in device memory.  counters[q]
 // serves the steps of parity q; each launch zeroes the other one for the next.
 template <int NW>
 __global__ void __launch_bounds__(32 * NW, 1)
@@ -682,7 +685,10 @@ __global__ void __launch_bounds__(32 * NW, 1)
             }
         }
         __syncthreads();
-        step_tile<NW, float>(sP, nullptr, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
+        // the grid's tensor maps live in device memory, written before the launch
+        const TileMaps* maps = &insts[tl.x].maps[parity];
+        if (tid == 0) fence_tensormap_acquire(maps);
+        step_tile<NW, float>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
                              partials + 2 * k);
     }
     if (blockIdx.x == 0 && tid == 0) *t_out = t + 1;
