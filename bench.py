@@ -264,7 +264,7 @@ def run_gpu(args, w, storage: str, rank: int, world: int, dist):
     sim.close()
     return {"ms": ms, "launches": launches, "clocks": sampler.summary(), "finite": ok,
             "shape": {"block_warps": shape[0], "tile_z": shape[1]} if shape else
-            {"block_warps": args.block_warps or 12, "tile_z": args.tile_z or 32}}
+            {"block_warps": args.block_warps or 8, "tile_z": args.tile_z or 0}}
 
 
 def run_batched(args):
@@ -318,14 +318,17 @@ def run_batched(args):
                         "and jets (D = 0.15 edge, periodic sides), We log-uniform in [10, 2000], seed 4"}
 
 
-def run_e2e(args, w, storage: str, world: int = 1, dist=None):
+def run_e2e(args, w, storage: str, world: int = 1, dist=None, shape=None):
     """Same metric through the public C ABI with host buffers: upload the
     initial fields from pinned memory, run the steps, read the moments, the
-    phase field and the FP64 sums back into pinned memory."""
+    phase field and the FP64 sums back into pinned memory.  `shape` is the
+    tile shape of the device-timed run (so both time the same kernel)."""
     import torch
     import paper_2403_15773_gb300 as tslb
     stream = torch.cuda.Stream()
-    sim = tslb.Simulation(w, storage=storage, stream=stream)
+    shape = shape or {}
+    sim = tslb.Simulation(w, storage=storage, stream=stream, block_warps=shape.get("block_warps", 0),
+                          tile_z=shape.get("tile_z", 0))
     N = w.nodes
     rho, u, phi = (torch.from_numpy(a.astype(np.float32).reshape(-1)).pin_memory() for a in w.fields())
     out_rho = torch.empty(N, dtype=torch.float32).pin_memory()
@@ -468,7 +471,7 @@ def main():
         variants["two_sweep"]["note"] = ("the paper's design on this GPU: collide+push into 34 population "
                                          "arrays, then their moments; fused speedup over it = "
                                          f"{base_glups / variants['two_sweep']['value']:.2f}x")
-    e2e = None if args.no_e2e else run_e2e(args, w, args.storage, world, dist)
+    e2e = None if args.no_e2e else run_e2e(args, w, args.storage, world, dist, res["shape"])
     if dist is not None:
         dist.barrier()
     if rank != 0:

@@ -126,6 +126,9 @@ typedef struct {
                                radial profiles of <phi> and <u_z>); 0 = off (default) */
     int32_t closure;        /* tslb_closure of the non-equilibrium second moment; default
                                TSLB_CLOSURE_PROJECTION */
+    int32_t test_tma_stall; /* testing only: 1 makes the step kernel's TMA tiles wait for bytes no copy
+                               delivers, so its bounded wait expires (about 1 s per block) and
+                               tslb_sums returns TSLB_ERR_TIMEOUT; 0 = off (default) */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
                                (blocking, so ordered with the legacy default stream) */
 } tslb_options;

@@ -64,7 +64,7 @@ class Options(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("tile_z", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("block_warps", ctypes.c_int32),
                 ("scheme", ctypes.c_int32), ("average", ctypes.c_int32), ("closure", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("test_tma_stall", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
 class TslbError(RuntimeError):
@@ -322,7 +322,8 @@ class Simulation:
 
     def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
                  graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0,
-                 average: bool = False, scheme: str = "fused", closure: str = "projection"):
+                 average: bool = False, scheme: str = "fused", closure: str = "projection",
+                 test_tma_stall: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Simulation needs a CUDA device")
@@ -341,6 +342,7 @@ class Simulation:
         o.average = 1 if average else 0
         o.scheme = {"fused": 0, "two_sweep": 1}[scheme]
         o.closure = CLOSURES[closure]
+        o.test_tma_stall = 1 if test_tma_stall else 0
         self.closure = closure
         if field_scale is not None:
             for g in range(4):

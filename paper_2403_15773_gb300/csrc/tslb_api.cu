@@ -181,6 +181,7 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     for (int k = 0; k < 6; ++k) p.face[k] = b.face[k];
     p.block_warps = opt->block_warps > 0 ? opt->block_warps : 8;
     p.closure = opt->closure;
+    p.test_stall = opt->test_tma_stall ? 1 : 0;
     p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz)
                                : auto_tile_z(grid, p.block_warps, 152);
     const long long N = (long long)grid->nx * grid->ny * grid->nz;

@@ -43,6 +43,7 @@ struct StepParams {
     float inv_scale[NFIELDS];
     double* avg;             // time sums of phi and u_z (2 blocks of fstride doubles) or null
     int* err;                // set to 1 by a kernel whose bounded wait for its tile data gave up
+    int test_stall;          // testing: TMA tiles expect bytes no copy delivers (the wait expires)
 };
 
 // Tensor maps of one step for the TMA tile copies of the step kernel: the 10

@@ -321,7 +321,8 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         }
         if (tid == 0) {
             fence_proxy_async();
-            mbar_expect_tx(bar + BPRO, bytes + PF * (unsigned)L::MOM_BOX);
+            // (P.test_stall: 16 bytes more than the copies deliver, so the wait below expires)
+            mbar_expect_tx(bar + BPRO, bytes + PF * (unsigned)L::MOM_BOX + (P.test_stall ? 16u : 0u));
             for (int q = z0 - 2; q <= z0 + PF; ++q) {
                 inl = 0;
                 const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);

@@ -331,6 +331,29 @@ def test_non_finite_state_is_reported():
     s2.close()
 
 
+def test_bounded_tma_wait_reports_timeout():
+    """Failure detection of the tile loads without any GPU fault: with the
+    testing option the TMA mbarrier of a tile expects 16 bytes more than its
+    copies deliver, so the kernel's bounded wait expires (about 1 s), the block
+    finishes without further waits, and tslb_sums reports TSLB_ERR_TIMEOUT.
+    All copies have landed when the block exits; a new context then steps
+    normally on the same device."""
+    w = inputs.jet_workload(28, 14, 8, diameter=6, noise=0.0, seed=2, steps=1)
+    rho, u, phi = w.fields()
+    sim = tslb.Simulation(w, block_warps=8, graph_steps=1, test_tma_stall=True)
+    sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+    sim.step(1)
+    with pytest.raises(tslb.TslbError) as ei:
+        sim.sums()
+    assert ei.value.status == tslb.TSLB_ERR_TIMEOUT
+    sim.close()
+    g, sums, launches = gpu_run(w, 3, block_warps=8)
+    assert launches == 3 and np.isfinite(sums[0]) and np.isfinite(sums[1])
+    r = oracle_sim(w)
+    r.step(3)
+    assert max(errors(g, r.moments())) < TOL
+
+
 @pytest.mark.parametrize("case", ["droplet", "jet"])
 def test_two_sweep_scheme_parity(case):
     """The paper's own two-sweep design (populations in HBM) matches the
