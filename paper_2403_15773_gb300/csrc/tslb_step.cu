@@ -212,24 +212,31 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     // imposed values are used directly).  Returns whether bar[kb] got copies.
     unsigned short rphi[EPT], rmom[2][10];
     auto issue = [&](bool do_p, int qp, bool do_m, int qm, int kb, float& sgz, int& inl) -> bool {
+        // only the inlet face is never loaded (its phase field is imposed)
+        const bool lp = do_p && !(inlet_face && qp < 0);
+        if (tma) {  // the issuing thread alone resolves the planes and addresses
+            if (tid == 0 && (lp || do_m)) {
+                float sg;
+                int in2 = 0;
+                fence_proxy_async();
+                mbar_expect_tx(bar + kb, (lp ? (unsigned)L::PHI_BOX : 0u) + (do_m ? (unsigned)L::MOM_BOX : 0u));
+                if (lp)
+                    tma_load_3d(ring + pslot(qp) * PSL, &maps->phi, xp, yp,
+                                resolve_axis(qp, nz, P.face[4], P.face[5], sg, in2), bar + kb);
+                if (do_m)
+                    tma_load_4d(momb + mslot(qm) * MSL, &maps->mom, xm, ym,
+                                resolve_axis(qm, nz, P.face[4], P.face[5], sg, in2), 0, bar + kb);
+            }
+            return lp || do_m;
+        }
         float sg;
         int inl_p = 0;
         const int szp = do_p ? resolve_axis(qp, nz, P.face[4], P.face[5], sg, inl_p) : 0;
         inl = 0;
         sgz = 1.f;
         const int szm = do_m ? resolve_axis(qm, nz, P.face[4], P.face[5], sgz, inl) : 0;
-        const bool lp = do_p && !inl_p;
         S* const pdst = ring + pslot(qp) * PSL;
         S* const mdst = momb + mslot(qm) * MSL;
-        if (tma) {
-            if (tid == 0 && (lp || do_m)) {
-                fence_proxy_async();
-                mbar_expect_tx(bar + kb, (lp ? (unsigned)L::PHI_BOX : 0u) + (do_m ? (unsigned)L::MOM_BOX : 0u));
-                if (lp) tma_load_3d(pdst, &maps->phi, xp, yp, szp, bar + kb);
-                if (do_m) tma_load_4d(mdst, &maps->mom, xm, ym, szm, 0, bar + kb);
-            }
-            return lp || do_m;
-        }
         if (lp) {
             const S* src = in + F_PHI * fs + nxy * szp;
 #pragma unroll
@@ -392,8 +399,10 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         const bool do_m = i + PF <= z1, do_p = i + 2 + PF <= z1 + 1;
         const int kb = bslot(i);
         if ((do_m || do_p) && issue(do_p, i + 2 + PF, do_m, i + PF, kb, sgz_nxt, inl_nxt)) pend |= 1u << kb;
-        cp_async_commit();
-        cp_async_wait<PF>();
+        if (!tma) {
+            cp_async_commit();
+            cp_async_wait<PF>();
+        }
         wait_bar(bslot(i + 1));  // == bslot(i - PF)
 
         float2 hYZ[9];
