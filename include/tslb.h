@@ -110,13 +110,15 @@ typedef struct {
                                scale * P, scale * phi; 0 = default (1/(3 U^2), 1/(2 U), 1e3, 1) */
     int32_t check_every;    /* tslb_step checks the FP64 sums for non-finite values every this
                                many steps (synchronises); 0 = never (default) */
-    int32_t tile_z;         /* z extent of one thread block's slab; 0 = automatic (64 planes, fewer
-                               for grids too small to fill the GPU) */
+    int32_t tile_z;         /* z extent of one thread block's slab; 0 = automatic (single grids: the
+                               depth in 8..128 minimising waves of one block per SM times the planes
+                               a block marches; batches: 64) */
     int32_t graph_steps;    /* steps per captured CUDA graph replayed by tslb_step; 0 = automatic,
                                1 = plain launches */
     int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 14, 22 or
                                30 interior rows; 28 interior columns with FP32 storage, 30 with
-                               16-bit storage or the Chapman-Enskog closure); 0 = 8 */
+                               16-bit storage or the Chapman-Enskog closure); 0 = 12 for a single
+                               grid, 8 for a batch */
     int32_t scheme;         /* 0: the fused moment-only step (default, 88 B per update in FP32);
                                1: the paper's two-sweep design kept as an ablation: collide+push
                                into 34 population arrays in HBM, then their moments (360 B per

@@ -77,14 +77,42 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t elem_size(int storage) { return storage == TSLB_FP32 ? 4 : 2; }
 
-// Default slab depth: 64 planes, halved while the grid would give fewer than
-// two blocks per SM (small grids need the parallelism more than the fewer
-// halo planes).
-int auto_tile_z(const tslb_grid* g, int nw, int sms) {
-    const long long tiles_xy = (long long)((g->nx + 29) / 30) * ((g->ny + 2 * nw - 3) / (2 * nw - 2));
-    int tz = 64;
-    while (tz > 8 && tiles_xy * ((g->nz + tz - 1) / tz) < 2LL * sms) tz /= 2;
-    return tz < g->nz ? tz : g->nz;
+// Interior columns of a tile (FP32 tiles of the projection step are 28
+// wide so that their store boxes start on 16-byte boundaries).
+int default_tile_width(const tslb_options* opt) {
+    return opt->storage == TSLB_FP32 && opt->closure == TSLB_CLOSURE_PROJECTION ? 28 : 30;
+}
+
+// SMs of the current device (152 if it cannot be queried).
+int device_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    return n;
+}
+
+// Default slab depth for blocks of nw warps and tiles tx columns wide: the
+// depth (8 .. 128 planes) that minimises (waves of one block per SM) x
+// (planes a block marches, its slab plus two halo planes), i.e. the time of
+// the last block to finish when every block takes the same time per plane.
+int auto_tile_z(const tslb_grid* g, int nw, int tx, int sms) {
+    const long long txy = (long long)((g->nx + tx - 1) / tx) * ((g->ny + 2 * nw - 3) / (2 * nw - 2));
+    int best = g->nz < 64 ? g->nz : 64;
+    long long best_cost = -1;
+    for (int tz = 8; tz <= 128; ++tz) {
+        const int d = tz < g->nz ? tz : g->nz;
+        const long long blocks = txy * ((g->nz + d - 1) / d);
+        const long long cost = ((blocks + sms - 1) / sms) * (d + 2);
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && d > best)) {
+            best_cost = cost;
+            best = d;
+        }
+        if (d == g->nz) break;
+    }
+    return best;
 }
 
 constexpr int kAutotuneTileZ[] = {16, 24, 32, 48, 64};
@@ -179,11 +207,11 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     p.ny = grid->ny;
     p.nz = grid->nz;
     for (int k = 0; k < 6; ++k) p.face[k] = b.face[k];
-    p.block_warps = opt->block_warps > 0 ? opt->block_warps : 8;
+    p.block_warps = opt->block_warps > 0 ? opt->block_warps : 12;
     p.closure = opt->closure;
     p.test_stall = opt->test_tma_stall ? 1 : 0;
     p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz)
-                               : auto_tile_z(grid, p.block_warps, 152);
+                               : auto_tile_z(grid, p.block_warps, default_tile_width(opt), device_sms());
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     p.fstride = (N + 63) / 64 * 64;
     p.omega = (float)omega;
