@@ -2,14 +2,18 @@
 // (arXiv 2403.15773) for sm_103a, and the small kernels around it.
 //
 // One launch = one time step over the whole grid.  Each thread block owns a
-// slab of 30 x TY interior columns and marches through its z range plane by
-// plane.  A warp holds one row of 32 staged columns (30 interior + 2 halo);
-// the block holds TY interior rows plus one halo row above and below.
+// slab of TX x TY interior columns (TX = 28 with FP32 storage, 30 with 16-bit
+// storage) and marches through its z range plane by plane.  A warp holds two
+// rows of 32 staged columns (interior + halo); the block holds TY interior
+// rows plus one halo row above and below.
 //
 // Per staged node and plane the kernel
 //   1. reads the moments (rho - 1, u, P) and the phase field of the node and of
-//      its ghost images (cp.async prefetch one plane ahead; ghosts follow the
-//      face rules: wrap, mirror, zero-gradient copy, jet inlet);
+//      its ghost images: one thread loads each plane's boxes with TMA
+//      (cp.async.bulk.tensor, mbarrier completion) a plane or two ahead, and
+//      ghosts of mirror / copy faces read their source inside the box; tiles
+//      whose ghost sources leave the box (periodic wraps) load element by
+//      element (cp.async, or 16-bit loads through registers);
 //   2. evaluates grad phi and its Hessian with the isotropic D3Q27 stencils,
 //      the normal n, the curvature kappa = div n and the surface-tension force
 //      F = -(sigma/2) kappa grad phi (Sec. 2.2);
@@ -30,7 +34,9 @@
 //      rho' = sum_i f_i(x - c_i), j' = sum_i c_i f_i(x - c_i),
 //      Pi' = sum_i c_i c_i f_i(x - c_i) up to FP32 rounding;
 //   5. stores rho' - 1, u' = j'/rho', P' = Pi' - rho' cs2 I - rho' u' u' and
-//      phi', and accumulates the FP64 block partials of sum(rho - 1), sum(phi).
+//      phi' (FP32: into a staging box that leaves by one TMA store per plane;
+//      16-bit: plain stores), and accumulates the FP64 block partials of
+//      sum(rho - 1), sum(phi).
 //
 // All arithmetic is FP32 and works with deviations from the rest state
 // (rho - 1, Pi - cs2 I) so that no O(1) terms cancel.
@@ -211,7 +217,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     // until commit().  Inlet planes of the phase field are never loaded (the
     // imposed values are used directly).  Returns whether bar[kb] got copies.
     unsigned short rphi[EPT], rmom[2][10];
-    auto issue = [&](bool do_p, int qp, bool do_m, int qm, int kb, float& sgz, int& inl) -> bool {
+    auto issue = [&](bool do_p, int qp, bool do_m, int qm, int kb) -> bool {
         // only the inlet face is never loaded (its phase field is imposed)
         const bool lp = do_p && !(inlet_face && qp < 0);
         if (tma) {  // the issuing thread alone resolves the planes and addresses
@@ -230,11 +236,9 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
             return lp || do_m;
         }
         float sg;
-        int inl_p = 0;
-        const int szp = do_p ? resolve_axis(qp, nz, P.face[4], P.face[5], sg, inl_p) : 0;
-        inl = 0;
-        sgz = 1.f;
-        const int szm = do_m ? resolve_axis(qm, nz, P.face[4], P.face[5], sgz, inl) : 0;
+        int in2 = 0;
+        const int szp = do_p ? resolve_axis(qp, nz, P.face[4], P.face[5], sg, in2) : 0;
+        const int szm = do_m ? resolve_axis(qm, nz, P.face[4], P.face[5], sg, in2) : 0;
         S* const pdst = ring + pslot(qp) * PSL;
         S* const mdst = momb + mslot(qm) * MSL;
         if (lp) {
@@ -315,43 +319,35 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     };
 
     // prologue: phase field at planes z0-2 .. z0+PF, moments at planes z0-1 .. z0+PF-2
-    float sgz_cur = 1.f, sgz_nxt = 1.f;
-    int inl_cur = 0, inl_nxt = 0;
+    float sgz_cur = 1.f;
+    int inl_cur = 0;
     if (tma) {
-        float sg;
-        int inl;
-        unsigned bytes = 0;
-        for (int q = z0 - 2; q <= z0 + PF; ++q) {
-            inl = 0;
-            resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);
-            if (!inl) bytes += (unsigned)L::PHI_BOX;
-        }
         if (tid == 0) {
+            float sg;
+            int in2 = 0;
+            unsigned bytes = PF * (unsigned)L::MOM_BOX;
+            for (int q = z0 - 2; q <= z0 + PF; ++q)
+                if (!(inlet_face && q < 0)) bytes += (unsigned)L::PHI_BOX;
             fence_proxy_async();
             // (P.test_stall: 16 bytes more than the copies deliver, so the wait below expires)
-            mbar_expect_tx(bar + BPRO, bytes + PF * (unsigned)L::MOM_BOX + (P.test_stall ? 16u : 0u));
-            for (int q = z0 - 2; q <= z0 + PF; ++q) {
-                inl = 0;
-                const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);
-                if (!inl) tma_load_3d(ring + pslot(q) * PSL, &maps->phi, xp, yp, sz, bar + BPRO);
-            }
-            for (int k = 0; k < PF; ++k) {
-                const int q = z0 - 1 + k;
-                const int sz = resolve_axis(q, nz, P.face[4], P.face[5], sg, inl);
-                tma_load_4d(momb + mslot(q) * MSL, &maps->mom, xm, ym, sz, 0, bar + BPRO);
-            }
+            mbar_expect_tx(bar + BPRO, bytes + (P.test_stall ? 16u : 0u));
+            for (int q = z0 - 2; q <= z0 + PF; ++q)
+                if (!(inlet_face && q < 0))
+                    tma_load_3d(ring + pslot(q) * PSL, &maps->phi, xp, yp,
+                                resolve_axis(q, nz, P.face[4], P.face[5], sg, in2), bar + BPRO);
+            for (int k = 0; k < PF; ++k)
+                tma_load_4d(momb + mslot(z0 - 1 + k) * MSL, &maps->mom, xm, ym,
+                            resolve_axis(z0 - 1 + k, nz, P.face[4], P.face[5], sg, in2), 0, bar + BPRO);
         }
         pend |= 1u << BPRO;
     } else {
-        float sg;
-        int inl;
         for (int q = z0 - 2; q <= z0 + PF; ++q) {
-            issue(true, q, false, 0, BPRO, sg, inl);
+            issue(true, q, false, 0, BPRO);
             commit(true, q, false, 0);
         }
 #pragma unroll
         for (int k = 0; k < PF; ++k) {
-            issue(false, 0, true, z0 - 1 + k, BPRO, sg, inl);
+            issue(false, 0, true, z0 - 1 + k, BPRO);
             commit(false, 0, true, z0 - 1 + k);
         }
     }
@@ -398,7 +394,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         }
         const bool do_m = i + PF <= z1, do_p = i + 2 + PF <= z1 + 1;
         const int kb = bslot(i);
-        if ((do_m || do_p) && issue(do_p, i + 2 + PF, do_m, i + PF, kb, sgz_nxt, inl_nxt)) pend |= 1u << kb;
+        if ((do_m || do_p) && issue(do_p, i + 2 + PF, do_m, i + PF, kb)) pend |= 1u << kb;
         if (!tma) {
             cp_async_commit();
             cp_async_wait<PF>();
