@@ -77,10 +77,10 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t elem_size(int storage) { return storage == TSLB_FP32 ? 4 : 2; }
 
-// Interior columns of a tile (FP32 tiles of the projection step are 28
-// wide so that their store boxes start on 16-byte boundaries).
+// Interior columns of a tile: 28 for the projection step, 30 for the
+// Chapman-Enskog step.
 int default_tile_width(const tslb_options* opt) {
-    return opt->storage == TSLB_FP32 && opt->closure == TSLB_CLOSURE_PROJECTION ? 28 : 30;
+    return opt->closure == TSLB_CLOSURE_PROJECTION ? 28 : 30;
 }
 
 // SMs of the current device (152 if it cannot be queried).

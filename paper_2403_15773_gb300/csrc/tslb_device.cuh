@@ -292,13 +292,49 @@ __device__ __forceinline__ void xsweep2_0(float2 k0, float2& m0, float2& m1, flo
 __device__ __forceinline__ float2 s0v(float2 a, float2 b, float2 c) { return mad(4.f, b, a + c); }
 __device__ __forceinline__ float2 l2v(float2 a, float2 b, float2 c) { return mad(-2.f, b, a + c); }
 
+// Interface terms of a node pair from the y combinations of the phase field
+// at the columns x - 1, x, x + 1 (index 0, 1, 2): S = 4 c + (c(+1) + c(-1)),
+// D = c(+1) - c(-1), L = (c(+1) + c(-1)) - 2 c, applied along y to the z
+// combinations {S, D, L} (yS = S_y S_z, yDS = D_y S_z, yLS = L_y S_z,
+// ySD = S_y D_z, yDD = D_y D_z, ySL = S_y L_z).  The isotropic D3Q27 stencils
+// are kept unscaled: G = 72 grad phi, Hd = 36 H_aa, Ho = 24 H_ab.  Then the
+// regularised normal n = grad phi / sqrt(|grad phi|^2 + eps^2) = G / |G|_eps
+// (eps scaled by 72), the curvature kappa = div n = (tr H - n.H.n) / |grad phi|
+// and the CSF force F = -(sigma/2) kappa grad phi (Sec. 2.2) become
+//   F = (sig_half / 36) (tr Hd - G.H'.G / |G|^2) / |G| * G,
+// where sig_half = -sigma/2 and H' weighs the off-diagonal terms 2 * 36 / 24.
+__device__ __forceinline__ void interface_x(const float2 (&yS)[3], const float2 (&yDS)[3], const float2 (&yLS)[3],
+                                            const float2 (&ySD)[3], const float2 (&yDD)[3], const float2 (&ySL)[3],
+                                            float sig_half, float eps2, float2& Fx, float2& Fy, float2& Fz,
+                                            float2& nxv, float2& nyv, float2& nzv) {
+    const float2 gx = yS[2] - yS[0];
+    const float2 gy = s0v(yDS[0], yDS[1], yDS[2]);
+    const float2 gz = s0v(ySD[0], ySD[1], ySD[2]);
+    const float2 hxx = l2v(yS[0], yS[1], yS[2]);
+    const float2 hyy = s0v(yLS[0], yLS[1], yLS[2]);
+    const float2 hzz = s0v(ySL[0], ySL[1], ySL[2]);
+    const float2 hxy = yDS[2] - yDS[0];
+    const float2 hxz = ySD[2] - ySD[0];
+    const float2 hyz = s0v(yDD[0], yDD[1], yDD[2]);
+
+    const float2 m2 = mad(gx, gx, mad(gy, gy, mad(gz, gz, bc(72.f * 72.f * eps2))));
+    const float2 im = make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
+    nxv = gx * im;
+    nyv = gy * im;
+    nzv = gz * im;
+    const float2 ghg = mad(gx, mad(gx, hxx, 3.f * mad(gy, hxy, gz * hxz)),
+                           mad(gy, mad(gy, hyy, 3.f * (gz * hyz)), gz * gz * hzz));
+    const float2 fk = ((sig_half * (1.f / 36.f)) * im) * ((hxx + hyy + hzz) - ghg * (im * im));
+    Fx = fk * gx;
+    Fy = fk * gy;
+    Fz = fk * gz;
+}
+
 // Interface terms of the staged row pair (tile rows 2w and 2w+1; .x / .y),
 // from the z combinations of the phase field of the pair's plane in `zb`
 // ([3][NPH]: phi, phi(z+1) + phi(z-1), phi(z+1) - phi(z-1), PHX columns,
-// halo 2): grad phi and its Hessian by the isotropic D3Q27 stencils (z
-// combos, then y combos for the row pair, then x combos), the regularised
-// normal n = grad phi / sqrt(|grad phi|^2 + eps^2), the curvature
-// kappa = div n and the CSF force F = -(sigma/2) kappa grad phi (Sec. 2.2).
+// halo 2): z combinations, then y combinations for the row pair, then
+// interface_x.
 template <int NPH>
 __device__ __forceinline__ void interface2(const float* zb, int lane, int w, float sig_half, float eps2,
                                            float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
@@ -327,85 +363,60 @@ __device__ __forceinline__ void interface2(const float* zb, int lane, int w, flo
     }
     const int ec = (lane + 1) + PHX * (2 * w + 1);
     phi = make_float2(zb[ec], zb[ec + PHX]);
-    const float2 gxp = (1.f / 72.f) * (yS[2] - yS[0]);
-    const float2 gyp = (1.f / 72.f) * s0v(yDS[0], yDS[1], yDS[2]);
-    const float2 gzp = (1.f / 72.f) * s0v(ySD[0], ySD[1], ySD[2]);
-    const float2 hxx = (1.f / 36.f) * l2v(yS[0], yS[1], yS[2]);
-    const float2 hyy = (1.f / 36.f) * s0v(yLS[0], yLS[1], yLS[2]);
-    const float2 hzz = (1.f / 36.f) * s0v(ySL[0], ySL[1], ySL[2]);
-    const float2 hxy = (1.f / 24.f) * (yDS[2] - yDS[0]);
-    const float2 hxz = (1.f / 24.f) * (ySD[2] - ySD[0]);
-    const float2 hyz = (1.f / 24.f) * s0v(yDD[0], yDD[1], yDD[2]);
+    interface_x(yS, yDS, yLS, ySD, yDD, ySL, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv);
+}
 
-    const float2 m2 = mad(gxp, gxp, mad(gyp, gyp, mad(gzp, gzp, bc(eps2))));
-    const float2 im = make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
-    nxv = gxp * im;
-    nyv = gyp * im;
-    nzv = gzp * im;
-    const float2 ghg = mad(gxp, mad(gxp, hxx, 2.f * mad(gyp, hxy, gzp * hxz)),
-                           mad(gyp, mad(gyp, hyy, 2.f * (gzp * hyz)), gzp * gzp * hzz));
-    const float2 kappa = (hxx + hyy + hzz) * im - ghg * (im * im * im);
-    const float2 fk = sig_half * kappa;
-    Fx = fk * gxp;
-    Fy = fk * gyp;
-    Fz = fk * gzp;
+// The six y combinations of one phase-field column for the row pair, from
+// the z combinations {S, D, L} of rows 2w .. 2w+3 (scalar arithmetic: the
+// operands come from four different rows, packing them would cost moves).
+__device__ __forceinline__ void ycomb(const float (&zS)[4], const float (&zD)[4], const float (&zL)[4], float2& yS,
+                                      float2& yDS, float2& yLS, float2& ySD, float2& yDD, float2& ySL) {
+    yS = make_float2(fmaf(4.f, zS[1], zS[0] + zS[2]), fmaf(4.f, zS[2], zS[1] + zS[3]));
+    yDS = make_float2(zS[2] - zS[0], zS[3] - zS[1]);
+    yLS = make_float2(fmaf(-2.f, zS[1], zS[0] + zS[2]), fmaf(-2.f, zS[2], zS[1] + zS[3]));
+    ySD = make_float2(fmaf(4.f, zD[1], zD[0] + zD[2]), fmaf(4.f, zD[2], zD[1] + zD[3]));
+    yDD = make_float2(zD[2] - zD[0], zD[3] - zD[1]);
+    ySL = make_float2(fmaf(4.f, zL[1], zL[0] + zL[2]), fmaf(4.f, zL[2], zL[1] + zL[3]));
 }
 
 // Interface terms of the staged row pair as interface2, from z combinations
 // stored per phase-field element as float4 {S, D, L, phi} with
 // S = 4 phi + (phi(z+1) + phi(z-1)), D = phi(z+1) - phi(z-1),
-// L = (phi(z+1) + phi(z-1)) - 2 phi: one 16-byte load per element, the y
-// combinations of the two rows in scalar arithmetic (their operands come from
-// four different rows, so packing them would cost register moves), the x
-// combinations and the rest in packed FP32.  The arithmetic is that of
-// interface2, operation for operation.
+// L = (phi(z+1) + phi(z-1)) - 2 phi: one 16-byte load per element.  For
+// tiles of 28 interior columns, whose lanes 30 and 31 stage no node that a
+// stored node needs: each lane forms the y combinations of one column, its
+// own (lane 31: column 0, the left neighbour of lane 0), and takes those of
+// columns x -+ 1 from its neighbour lanes (a third of the loads and y
+// arithmetic of forming all three columns, for 24 shuffles).
 template <int NPH>
 __device__ __forceinline__ void interface4(const float4* zb, int lane, int w, float sig_half, float eps2,
-                                           float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
-                                           float2& nyv, float2& nzv) {
-    float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
+                                            float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
+                                            float2& nyv, float2& nzv) {
+    float zS[4], zD[4], zL[4];
+    const int col = lane == 31 ? 0 : lane + 1;
 #pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-        float zS[4], zD[4], zL[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float4 v = zb[(lane + 1 + dx) + PHX * (2 * w + r)];
-            zS[r] = v.x;
-            zD[r] = v.y;
-            zL[r] = v.z;
-            if (dx == 0 && r == 1) phi.x = v.w;
-            if (dx == 0 && r == 2) phi.y = v.w;
-        }
-        const int k = dx + 1;
-        yS[k] = make_float2(fmaf(4.f, zS[1], zS[0] + zS[2]), fmaf(4.f, zS[2], zS[1] + zS[3]));
-        yDS[k] = make_float2(zS[2] - zS[0], zS[3] - zS[1]);
-        yLS[k] = make_float2(fmaf(-2.f, zS[1], zS[0] + zS[2]), fmaf(-2.f, zS[2], zS[1] + zS[3]));
-        ySD[k] = make_float2(fmaf(4.f, zD[1], zD[0] + zD[2]), fmaf(4.f, zD[2], zD[1] + zD[3]));
-        yDD[k] = make_float2(zD[2] - zD[0], zD[3] - zD[1]);
-        ySL[k] = make_float2(fmaf(4.f, zL[1], zL[0] + zL[2]), fmaf(4.f, zL[2], zL[1] + zL[3]));
+    for (int r = 0; r < 4; ++r) {
+        const float4 v = zb[col + PHX * (2 * w + r)];
+        zS[r] = v.x;
+        zD[r] = v.y;
+        zL[r] = v.z;
+        if (r == 1) phi.x = v.w;
+        if (r == 2) phi.y = v.w;
     }
-    const float2 gxp = (1.f / 72.f) * (yS[2] - yS[0]);
-    const float2 gyp = (1.f / 72.f) * s0v(yDS[0], yDS[1], yDS[2]);
-    const float2 gzp = (1.f / 72.f) * s0v(ySD[0], ySD[1], ySD[2]);
-    const float2 hxx = (1.f / 36.f) * l2v(yS[0], yS[1], yS[2]);
-    const float2 hyy = (1.f / 36.f) * s0v(yLS[0], yLS[1], yLS[2]);
-    const float2 hzz = (1.f / 36.f) * s0v(ySL[0], ySL[1], ySL[2]);
-    const float2 hxy = (1.f / 24.f) * (yDS[2] - yDS[0]);
-    const float2 hxz = (1.f / 24.f) * (ySD[2] - ySD[0]);
-    const float2 hyz = (1.f / 24.f) * s0v(yDD[0], yDD[1], yDD[2]);
-
-    const float2 m2 = mad(gxp, gxp, mad(gyp, gyp, mad(gzp, gzp, bc(eps2))));
-    const float2 im = make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
-    nxv = gxp * im;
-    nyv = gyp * im;
-    nzv = gzp * im;
-    const float2 ghg = mad(gxp, mad(gxp, hxx, 2.f * mad(gyp, hxy, gzp * hxz)),
-                           mad(gyp, mad(gyp, hyy, 2.f * (gzp * hyz)), gzp * gzp * hzz));
-    const float2 kappa = (hxx + hyy + hzz) * im - ghg * (im * im * im);
-    const float2 fk = sig_half * kappa;
-    Fx = fk * gxp;
-    Fy = fk * gyp;
-    Fz = fk * gzp;
+    float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
+    ycomb(zS, zD, zL, yS[1], yDS[1], yLS[1], ySD[1], yDD[1], ySL[1]);
+    const int left = (lane + 31) & 31;
+    auto nb = [&](float2 (&y)[3]) {
+        y[0] = make_float2(__shfl_sync(FULL, y[1].x, left), __shfl_sync(FULL, y[1].y, left));
+        y[2] = shfl_down2(y[1]);
+    };
+    nb(yS);
+    nb(yDS);
+    nb(yLS);
+    nb(ySD);
+    nb(yDD);
+    nb(ySL);
+    interface_x(yS, yDS, yLS, ySD, yDD, ySL, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv);
 }
 
 // Collision and x sweep of a node pair.  Builds the post-collision Hermite

@@ -2,8 +2,8 @@
 // (arXiv 2403.15773) for sm_103a, and the small kernels around it.
 //
 // One launch = one time step over the whole grid.  Each thread block owns a
-// slab of TX x TY interior columns (TX = 28 with FP32 storage, 30 with 16-bit
-// storage) and marches through its z range plane by plane.  A warp holds two
+// slab of 28 x TY interior columns and marches through its z range plane by
+// plane.  A warp holds two
 // rows of 32 staged columns (interior + halo); the block holds TY interior
 // rows plus one halo row above and below.
 //
@@ -61,11 +61,12 @@ struct Step2Smem {
     static constexpr int TY = NR - 2;                        // interior rows
     static constexpr int NPH = PHX * (NR + 2);               // phase-field elements (halo 2)
     static constexpr int AL = 16 / (int)sizeof(S);           // elements per 16 bytes
-    // interior columns of a tile: FP32 tiles start on 16-byte boundaries (28
-    // columns) so that finished planes leave by TMA store; 16-bit tiles are 30
-    // wide (a 16-byte store box would be 24 columns) and use plain stores
+    // interior columns of a tile: 28, so that the staged columns (interior and
+    // one halo column each side) leave lanes 30 and 31 spare for the interface
+    // stencil's neighbour columns, and FP32 tiles start on 16-byte boundaries
+    // (finished planes leave by TMA store; 16-bit storage uses plain stores)
     static constexpr bool kFp32 = sizeof(S) == 4;
-    static constexpr int TXS = kFp32 ? 28 : 30;
+    static constexpr int TXS = 28;
     // (16-warp blocks have no room for the staging boxes: plain stores)
     static constexpr bool kTmaStore = kFp32 && NW <= 12;
     // box columns: staged columns x0-1 .. x0+30 (moments) and x0-2 .. x0+31
@@ -86,8 +87,8 @@ struct Step2Smem {
     static constexpr size_t MOM = 0;                                 // [MS] moment boxes
     static constexpr size_t RING = MOM + MS * MOM_SLOT;              // [PS] phase-field boxes
     static constexpr int EPT = (NPH + NT - 1) / NT;                  // phase-field elements per thread
-    static constexpr size_t ZC = RING + PS * PHI_SLOT;               // [EPT * NT] float4 z combinations
-    static constexpr size_t YX = ZC + 16 * (size_t)EPT * NT;         // [20][NT] float y exchange
+    static constexpr size_t ZC = RING + PS * PHI_SLOT;               // [2][EPT * NT] float4 z combinations
+    static constexpr size_t YX = ZC + 2 * 16 * (size_t)EPT * NT;     // [20][NT] float y exchange
     static constexpr size_t OUT_BOX = kTmaStore ? sizeof(float) * NFIELDS * TY * TXS : 0;  // [11][TY][TXS]
     static constexpr size_t OUT_SLOT = r128(OUT_BOX);
     static constexpr size_t OUT = r128(YX + sizeof(float) * 20 * NT);  // [2] output staging boxes
@@ -106,7 +107,7 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
     return p + ((0u - smem_u32(p)) & 127u);
 }
 
-// One tile of one time step: the 30 x (2 NW - 2) interior columns at tile
+// One tile of one time step: the 28 x (2 NW - 2) interior columns at tile
 // (bx, by), planes [bz * tile_z, (bz + 1) * tile_z), from state `in` (step t)
 // to state `out`; writes the tile's FP64 partial sums to part[0..1].
 // maps: tensor maps of `in` for TMA loads, or null (element-wise loads).
@@ -300,7 +301,10 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         pend &= ~(1u << kb);
     };
     // z combinations {S, D, L, phi} of the phase field at plane q from the
-    // ring planes q - 1, q, q + 1 (see interface4); inlet planes are imposed
+    // ring planes q - 1, q, q + 1 (see interface4) into the z-combination
+    // buffer of q's parity; inlet planes are imposed.  Each thread combines
+    // the phase-field elements it loads itself (element-wise loads need no
+    // barrier before it).
     auto zcombine = [&](int q) {
         const S* pm = ring + pslot(q - 1) * PSL;
         const S* pc = ring + pslot(q) * PSL;
@@ -314,7 +318,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
             const float b = ic ? phib[e] : Io<S>::cvt(pc[prd[e]], inv);
             const float c = Io<S>::cvt(pp[prd[e]], inv);
             const float s = c + a;
-            zc[tid + e * NT] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
+            zc[((q + 8) & 1) * (EPT * NT) + tid + e * NT] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
         }
     };
 
@@ -372,14 +376,18 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     const float sig_half = -0.5f * P.sigma;
 
     // March over planes i = z0 - 1 .. z1 with two barriers per plane:
-    //   B: the z combinations of plane i are complete, the y exchange of the
-    //      previous plane has been read, the slots loaded next are free;
+    //   B: the y exchange of the previous plane has been read, the ring and
+    //      moment slots loaded next and the z-combination buffer written
+    //      next are free;
     //   loads of phi(i + 2 + PF) and the moments of i + PF; wait for those of
     //      phi(i + 2) and the moments of i (issued PF planes earlier);
-    //   (d) stencils, collision, x sweep and y populations of plane i;
-    //   A: the y exchange of plane i is complete;
+    //   (d) stencils of plane i, z combinations of plane i + 1 (ring planes
+    //      i .. i + 2, into the other z-combination buffer; 16-warp blocks at
+    //      the end of (e)), collision, x sweep and y populations of plane i;
+    //   A: the y exchange of plane i and the z combinations of i + 1 are
+    //      complete;
     //   (e) y shift and moments, z shift and moments of plane i, output of
-    //      plane i - 1; z combinations of plane i + 1 (ring planes i .. i + 2).
+    //      plane i - 1.
     // The values (d) hands to (e) live in registers only across barrier A.
     for (int i = z0 - 1; i <= z1; ++i) {
         if (__syncthreads_or(dead)) break;
@@ -428,10 +436,17 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
 
             // interface terms from the z combinations of phi at plane i
             float2 phi, Fx, Fy, Fz, nxv, nyv, nzv;
-            interface4<NPH>(zc, lane, w, sig_half, P.normal_eps2, phi, Fx, Fy, Fz, nxv, nyv, nzv);
+            const float4* zci = zc + ((i + 8) & 1) * (EPT * NT);
+            static_assert(TX <= 28, "the interface stencil takes columns from the spare lanes 30, 31");
+            interface4<NPH>(zci, lane, w, sig_half, P.normal_eps2, phi, Fx, Fy, Fz, nxv, nyv, nzv);
             if (inl_cur) {
                 Fx = Fy = Fz = bc(0.f);
                 nxv = nyv = nzv = bc(0.f);
+            }
+            // shared-memory work of the next plane amid the arithmetic of this one
+            // (16-warp blocks, at 128 registers, do it in (e): here it spills)
+            if constexpr (NW <= 12) {
+                if (i < z1) zcombine(i + 1);
             }
 
             // Guo forcing: v = u + F / (2 rho)
@@ -602,7 +617,9 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         }
 
         if (tst) fence_proxy_async();  // the staging box is read by the TMA store next iteration
-        if (i < z1) zcombine(i + 1);
+        if constexpr (NW > 12) {
+            if (i < z1) zcombine(i + 1);
+        }
         commit(do_p, i + 2 + PF, do_m, i + PF);
     }
     // the last plane (z1 - 1) waits in its staging box
@@ -903,11 +920,9 @@ LaunchShape step_shape(const StepParams& p, int storage) {
     LaunchShape sh;
     sh.nw = p.block_warps;
     const int ty = 2 * sh.nw - 2;
-    // tile width: the projection step's FP32 tiles are 16-byte aligned (28), the
-    // rest (16-bit storage, the Chapman-Enskog step) 30 columns
-    const int tx = p.closure == CL_CHAPMAN_ENSKOG ? TX
-                   : storage == ST_FP32           ? Step2Smem<8, float>::TXS
-                                                  : Step2Smem<8, __half>::TXS;
+    // tile width: 28 columns for the projection step, 30 for the Chapman-Enskog step
+    const int tx = p.closure == CL_CHAPMAN_ENSKOG ? TX : Step2Smem<8, float>::TXS;
+    static_assert(Step2Smem<8, float>::TXS == Step2Smem<8, __half>::TXS, "one tile width per closure");
     sh.grid = dim3((p.nx + tx - 1) / tx, (p.ny + ty - 1) / ty, (p.nz + p.tile_z - 1) / p.tile_z);
     sh.block = dim3(32, sh.nw, 1);
     sh.smem = step_smem_bytes(sh.nw, storage);
