@@ -116,8 +116,7 @@ typedef struct {
     int32_t graph_steps;    /* steps per captured CUDA graph replayed by tslb_step; 0 = automatic,
                                1 = plain launches */
     int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 14, 22 or
-                               30 interior rows; 28 interior columns, 30 with the Chapman-Enskog
-                               closure); 0 = 12 for a single
+                               30 interior rows; 28 interior columns); 0 = 12 for a single
                                grid, 8 for a batch */
     int32_t scheme;         /* 0: the fused moment-only step (default, 88 B per update in FP32);
                                1: the paper's two-sweep design kept as an ablation: collide+push

@@ -77,11 +77,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t elem_size(int storage) { return storage == TSLB_FP32 ? 4 : 2; }
 
-// Interior columns of a tile: 28 for the projection step, 30 for the
-// Chapman-Enskog step.
-int default_tile_width(const tslb_options* opt) {
-    return opt->closure == TSLB_CLOSURE_PROJECTION ? 28 : 30;
-}
+// Interior columns of a tile (every step kernel).
+int default_tile_width(const tslb_options*) { return 28; }
 
 // SMs of the current device (152 if it cannot be queried).
 int device_sms() {

@@ -15,8 +15,12 @@ namespace tslb {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int TX = 30;        // interior columns of a tile; a warp stages TX + 2
-constexpr int PHX = TX + 4;   // phase-field columns of a tile (halo 2)
+// Interior columns of a tile: lanes 1 .. 28 of a warp; lanes 0 and 29 stage
+// the halo columns, lanes 30 and 31 are spare (the stencils take neighbour
+// columns from neighbour lanes, lane 31 standing in for the column left of
+// lane 0).
+constexpr int TX = 28;
+constexpr int PHX = 34;       // footprint columns of a tile: x0 - 2 .. x0 + 31
 
 // ------------------------------------------------------------------ helpers
 
@@ -330,42 +334,6 @@ __device__ __forceinline__ void interface_x(const float2 (&yS)[3], const float2 
     Fz = fk * gz;
 }
 
-// Interface terms of the staged row pair (tile rows 2w and 2w+1; .x / .y),
-// from the z combinations of the phase field of the pair's plane in `zb`
-// ([3][NPH]: phi, phi(z+1) + phi(z-1), phi(z+1) - phi(z-1), PHX columns,
-// halo 2): z combinations, then y combinations for the row pair, then
-// interface_x.
-template <int NPH>
-__device__ __forceinline__ void interface2(const float* zb, int lane, int w, float sig_half, float eps2,
-                                           float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
-                                           float2& nyv, float2& nzv) {
-    float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-        float zS[4], zD[4], zL[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int e = (lane + 1 + dx) + PHX * (2 * w + r);
-            const float c0 = zb[e], c1 = zb[NPH + e], c2 = zb[2 * NPH + e];
-            zS[r] = fmaf(4.f, c0, c1);
-            zD[r] = c2;
-            zL[r] = fmaf(-2.f, c0, c1);
-        }
-        const float2 sm = make_float2(zS[0], zS[1]), s0 = make_float2(zS[1], zS[2]), sp = make_float2(zS[2], zS[3]);
-        const float2 dm = make_float2(zD[0], zD[1]), d0 = make_float2(zD[1], zD[2]), dp = make_float2(zD[2], zD[3]);
-        const float2 lm = make_float2(zL[0], zL[1]), l0 = make_float2(zL[1], zL[2]), lp = make_float2(zL[2], zL[3]);
-        yS[dx + 1] = s0v(sm, s0, sp);
-        yDS[dx + 1] = sp - sm;
-        yLS[dx + 1] = l2v(sm, s0, sp);
-        ySD[dx + 1] = s0v(dm, d0, dp);
-        yDD[dx + 1] = dp - dm;
-        ySL[dx + 1] = s0v(lm, l0, lp);
-    }
-    const int ec = (lane + 1) + PHX * (2 * w + 1);
-    phi = make_float2(zb[ec], zb[ec + PHX]);
-    interface_x(yS, yDS, yLS, ySD, yDD, ySL, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv);
-}
-
 // The six y combinations of one phase-field column for the row pair, from
 // the z combinations {S, D, L} of rows 2w .. 2w+3 (scalar arithmetic: the
 // operands come from four different rows, packing them would cost moves).
@@ -379,30 +347,15 @@ __device__ __forceinline__ void ycomb(const float (&zS)[4], const float (&zD)[4]
     ySL = make_float2(fmaf(4.f, zL[1], zL[0] + zL[2]), fmaf(4.f, zL[2], zL[1] + zL[3]));
 }
 
-// Interface terms of the staged row pair as interface2, from z combinations
-// stored per phase-field element as float4 {S, D, L, phi} with
-// S = 4 phi + (phi(z+1) + phi(z-1)), D = phi(z+1) - phi(z-1),
-// L = (phi(z+1) + phi(z-1)) - 2 phi: one 16-byte load per element.  For
-// tiles of 28 interior columns, whose lanes 30 and 31 stage no node that a
-// stored node needs: each lane forms the y combinations of one column, its
-// own (lane 31: column 0, the left neighbour of lane 0), and takes those of
-// columns x -+ 1 from its neighbour lanes (a third of the loads and y
-// arithmetic of forming all three columns, for 24 shuffles).
-template <int NPH>
-__device__ __forceinline__ void interface4(const float4* zb, int lane, int w, float sig_half, float eps2,
-                                            float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
-                                            float2& nyv, float2& nzv) {
-    float zS[4], zD[4], zL[4];
-    const int col = lane == 31 ? 0 : lane + 1;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const float4 v = zb[col + PHX * (2 * w + r)];
-        zS[r] = v.x;
-        zD[r] = v.y;
-        zL[r] = v.z;
-        if (r == 1) phi.x = v.w;
-        if (r == 2) phi.y = v.w;
-    }
+// Interface terms of the staged row pair from the z combinations {S, D, L}
+// of rows 2w .. 2w+3 of the lane's own footprint column (lane 31: column 0):
+// y combinations of that column, those of the columns x -+ 1 from the
+// neighbour lanes (a third of the loads and y arithmetic of forming all three
+// columns in every lane, for 24 shuffles), then interface_x.  Valid in lanes
+// 0 .. 29 (the staged columns of a 28-column tile).
+__device__ __forceinline__ void interface_nb(const float (&zS)[4], const float (&zD)[4], const float (&zL)[4],
+                                             int lane, float sig_half, float eps2, float2& Fx, float2& Fy,
+                                             float2& Fz, float2& nxv, float2& nyv, float2& nzv) {
     float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
     ycomb(zS, zD, zL, yS[1], yDS[1], yLS[1], ySD[1], yDD[1], ySL[1]);
     const int left = (lane + 31) & 31;
@@ -417,6 +370,53 @@ __device__ __forceinline__ void interface4(const float4* zb, int lane, int w, fl
     nb(yDD);
     nb(ySL);
     interface_x(yS, yDS, yLS, ySD, yDD, ySL, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv);
+}
+
+// Footprint column a lane forms its stencil values for: its own staged column
+// (footprint column lane + 1), lane 31 the column left of lane 0's.
+__device__ __forceinline__ int own_column(int lane) { return lane == 31 ? 0 : lane + 1; }
+
+// Interface terms of the staged row pair (tile rows 2w and 2w+1; .x / .y),
+// from z combinations stored per phase-field element as float4 {S, D, L, phi}
+// with S = 4 phi + (phi(z+1) + phi(z-1)), D = phi(z+1) - phi(z-1),
+// L = (phi(z+1) + phi(z-1)) - 2 phi: one 16-byte load per element.
+template <int NPH>
+__device__ __forceinline__ void interface4(const float4* zb, int lane, int w, float sig_half, float eps2,
+                                           float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
+                                           float2& nyv, float2& nzv) {
+    float zS[4], zD[4], zL[4];
+    const int col = own_column(lane);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float4 v = zb[col + PHX * (2 * w + r)];
+        zS[r] = v.x;
+        zD[r] = v.y;
+        zL[r] = v.z;
+        if (r == 1) phi.x = v.w;
+        if (r == 2) phi.y = v.w;
+    }
+    interface_nb(zS, zD, zL, lane, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv);
+}
+
+// The same from z combinations stored as three planes of the footprint
+// ([3][NPH]: phi, phi(z+1) + phi(z-1), phi(z+1) - phi(z-1)).
+template <int NPH>
+__device__ __forceinline__ void interface2(const float* zb, int lane, int w, float sig_half, float eps2,
+                                           float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
+                                           float2& nyv, float2& nzv) {
+    float zS[4], zD[4], zL[4];
+    const int col = own_column(lane);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = col + PHX * (2 * w + r);
+        const float c0 = zb[e], c1 = zb[NPH + e], c2 = zb[2 * NPH + e];
+        zS[r] = fmaf(4.f, c0, c1);
+        zD[r] = c2;
+        zL[r] = fmaf(-2.f, c0, c1);
+        if (r == 1) phi.x = c0;
+        if (r == 2) phi.y = c0;
+    }
+    interface_nb(zS, zD, zL, lane, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv);
 }
 
 // Collision and x sweep of a node pair.  Builds the post-collision Hermite

@@ -66,7 +66,7 @@ struct Step2Smem {
     // stencil's neighbour columns, and FP32 tiles start on 16-byte boundaries
     // (finished planes leave by TMA store; 16-bit storage uses plain stores)
     static constexpr bool kFp32 = sizeof(S) == 4;
-    static constexpr int TXS = 28;
+    static constexpr int TXS = TX;
     // (16-warp blocks have no room for the staging boxes: plain stores)
     static constexpr bool kTmaStore = kFp32 && NW <= 12;
     // box columns: staged columns x0-1 .. x0+30 (moments) and x0-2 .. x0+31
@@ -117,7 +117,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
                                           const int bz, double* __restrict__ part) {
     using L = Step2Smem<NW, S>;
     constexpr int NT = L::NT, NR = L::NR, NPH = L::NPH, MW = L::MW, PW = L::PW, FS = L::FS, AL = L::AL;
-    constexpr int TY = L::TY, TX = L::TXS;
+    constexpr int TY = L::TY;
     constexpr int OSL = (int)(L::OUT_SLOT / sizeof(float));
     constexpr int EPT = L::EPT;
     constexpr int MSL = (int)(L::MOM_SLOT / sizeof(S)), PSL = (int)(L::PHI_SLOT / sizeof(S));
@@ -920,9 +920,7 @@ LaunchShape step_shape(const StepParams& p, int storage) {
     LaunchShape sh;
     sh.nw = p.block_warps;
     const int ty = 2 * sh.nw - 2;
-    // tile width: 28 columns for the projection step, 30 for the Chapman-Enskog step
-    const int tx = p.closure == CL_CHAPMAN_ENSKOG ? TX : Step2Smem<8, float>::TXS;
-    static_assert(Step2Smem<8, float>::TXS == Step2Smem<8, __half>::TXS, "one tile width per closure");
+    const int tx = TX;  // 28 interior columns for every kernel
     sh.grid = dim3((p.nx + tx - 1) / tx, (p.ny + ty - 1) / ty, (p.nz + p.tile_z - 1) / p.tile_z);
     sh.block = dim3(32, sh.nw, 1);
     sh.smem = step_smem_bytes(sh.nw, storage);

@@ -350,23 +350,25 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
             const float2 uy = make_float2(jpl[2 * NPH + ec], jpl[2 * NPH + ec + PHX]) * irho;
             const float2 uz = make_float2(jpl[3 * NPH + ec], jpl[3 * NPH + ec + PHX]) * irho;
 
-            // strain rate: dA_b = 72 d_a j_b from the z combinations of plane i
+            // strain rate: dA_b = 72 d_a j_b from the z combinations of plane i.
+            // Each lane forms the y combinations S'_y S'_z j_b, D_y S'_z j_b and
+            // S'_y D_z j_b of its own footprint column (lane 31: column 0) and
+            // takes those of the columns x -+ 1 from its neighbour lanes:
+            //   dX_b = (S'S')(x+1) - (S'S')(x-1),
+            //   dY_b = (DS')(x-1) + 4 (DS')(x) + (DS')(x+1), dZ_b likewise with S'D.
             const float4* z4 = jz4 + ((i + 8) & 1) * NPH;
             const float2* z2 = jz2 + ((i + 8) & 1) * NPH;
-            float2 dXx = bc(0.f), dXy = bc(0.f), dXz = bc(0.f);
-            float2 dYx = bc(0.f), dYy = bc(0.f), dYz = bc(0.f);
-            float2 dZx = bc(0.f), dZy = bc(0.f), dZz = bc(0.f);
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
+            float2 SS[3], DS[3], SD[3];
+            {
+                const int col = own_column(lane);
                 float4 a[4];
                 float2 b[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const int e = (lane + 1 + dx) + PHX * (2 * w + r);
+                    const int e = col + PHX * (2 * w + r);
                     a[r] = z4[e];
                     b[r] = z2[e];
                 }
-                const float wx = dx == 0 ? 4.f : 1.f;
                 // S'_z j_b in a[].x/y/z; D_z j_b in a[].w, b[].x, b[].y
                 const float sv[3][4] = {{a[0].x, a[1].x, a[2].x, a[3].x},
                                         {a[0].y, a[1].y, a[2].y, a[3].y},
@@ -374,33 +376,31 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
                 const float dv[3][4] = {{a[0].w, a[1].w, a[2].w, a[3].w},
                                         {b[0].x, b[1].x, b[2].x, b[3].x},
                                         {b[0].y, b[1].y, b[2].y, b[3].y}};
-                float2 SS[3], DS[3], SD[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const float2 sm = make_float2(sv[k][0], sv[k][1]), s0 = make_float2(sv[k][1], sv[k][2]),
                                  sp = make_float2(sv[k][2], sv[k][3]);
                     const float2 dm = make_float2(dv[k][0], dv[k][1]), d0 = make_float2(dv[k][1], dv[k][2]),
                                  dp = make_float2(dv[k][2], dv[k][3]);
-                    SS[k] = dx == 0 ? bc(0.f) : s0v(sm, s0, sp);
+                    SS[k] = s0v(sm, s0, sp);
                     DS[k] = sp - sm;
                     SD[k] = s0v(dm, d0, dp);
                 }
-                if (dx != 0) {
-                    const float sgn = (float)dx;
-                    dXx = mad(sgn, SS[0], dXx);
-                    dXy = mad(sgn, SS[1], dXy);
-                    dXz = mad(sgn, SS[2], dXz);
-                }
-                dYx = mad(wx, DS[0], dYx);
-                dYy = mad(wx, DS[1], dYy);
-                dYz = mad(wx, DS[2], dYz);
-                dZx = mad(wx, SD[0], dZx);
-                dZy = mad(wx, SD[1], dZy);
-                dZz = mad(wx, SD[2], dZz);
+            }
+            const int left = (lane + 31) & 31;
+            auto from_left = [&](float2 v) {
+                return make_float2(__shfl_sync(FULL, v.x, left), __shfl_sync(FULL, v.y, left));
+            };
+            float2 dX[3], dY[3], dZ[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                dX[k] = shfl_down2(SS[k]) - from_left(SS[k]);
+                dY[k] = s0v(from_left(DS[k]), DS[k], shfl_down2(DS[k]));
+                dZ[k] = s0v(from_left(SD[k]), SD[k], shfl_down2(SD[k]));
             }
             const float2 c1 = bc(cce), c2 = bc(2.f * cce);
-            const float2 nxx = c2 * dXx, nyy = c2 * dYy, nzz = c2 * dZz;
-            const float2 nxy = c1 * (dXy + dYx), nxz = c1 * (dXz + dZx), nyz = c1 * (dYz + dZy);
+            const float2 nxx = c2 * dX[0], nyy = c2 * dY[1], nzz = c2 * dZ[2];
+            const float2 nxy = c1 * (dX[1] + dY[0]), nxz = c1 * (dX[2] + dZ[0]), nyz = c1 * (dY[2] + dZ[1]);
 
             // interface terms from the z combinations of phi at plane i
             float2 phi, Fx, Fy, Fz, nxv, nyv, nzv;
