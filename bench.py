@@ -232,7 +232,7 @@ def run_gpu(args, w, storage: str, rank: int, world: int, dist):
     two = scheme == "two_sweep"
     sim = tslb.Simulation(w, storage=st, stream=stream,
                           block_warps=0 if two else args.block_warps, tile_z=0 if two else args.tile_z,
-                          scheme=scheme, closure=closure)
+                          scheme=scheme, closure=closure, plain_stores=args.plain_stores and not two)
     rho, u, phi = w.fields()
     sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
     shape = None
@@ -263,8 +263,9 @@ def run_gpu(args, w, storage: str, rank: int, world: int, dist):
     ms = max_over_ranks(ms, dist, dev)  # the slowest rank sets the job's time
     sim.close()
     return {"ms": ms, "launches": launches, "clocks": sampler.summary(), "finite": ok,
-            "shape": {"block_warps": shape[0], "tile_z": shape[1]} if shape else
-            {"block_warps": args.block_warps or 8, "tile_z": args.tile_z or 0}}
+            "shape": {"block_warps": shape[0], "tile_z": shape[1], "plain_stores": shape[2]} if shape else
+            {"block_warps": args.block_warps or 8, "tile_z": args.tile_z or 0,
+             "plain_stores": int(args.plain_stores)}}
 
 
 def run_batched(args):
@@ -313,7 +314,8 @@ def run_batched(args):
             "unit": UNIT, "ms_per_step": ms_batch / steps,
             "hbm_frac": FIELDS * 8 * nodes / (ms_batch * 1e-3 / steps) / 1e9 / peak,
             "sequential_fp32_value": g_seq, "speedup_vs_sequential_fp32": g_batch / g_seq,
-            "gpu_launches": launches, "autotuned": {"block_warps": shape[0], "tile_z": shape[1]},
+            "gpu_launches": launches,
+            "autotuned": {"block_warps": shape[0], "tile_z": shape[1], "plain_stores": shape[2]},
             "workload": "64 cubic grids, edges uniform in {48, 64, 96, 128}, periodic droplets (R = edge/4) "
                         "and jets (D = 0.15 edge, periodic sides), We log-uniform in [10, 2000], seed 4"}
 
@@ -328,7 +330,7 @@ def run_e2e(args, w, storage: str, world: int = 1, dist=None, shape=None):
     stream = torch.cuda.Stream()
     shape = shape or {}
     sim = tslb.Simulation(w, storage=storage, stream=stream, block_warps=shape.get("block_warps", 0),
-                          tile_z=shape.get("tile_z", 0))
+                          tile_z=shape.get("tile_z", 0), plain_stores=bool(shape.get("plain_stores", 0)))
     N = w.nodes
     rho, u, phi = (torch.from_numpy(a.astype(np.float32).reshape(-1)).pin_memory() for a in w.fields())
     out_rho = torch.empty(N, dtype=torch.float32).pin_memory()
@@ -424,6 +426,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--block-warps", type=int, default=0)
     ap.add_argument("--tile-z", type=int, default=0)
+    ap.add_argument("--plain-stores", action="store_true",
+                    help="with --block-warps / --tile-z: the FP32 step kernel form without the store staging box")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

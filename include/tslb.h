@@ -130,6 +130,13 @@ typedef struct {
     int32_t test_tma_stall; /* testing only: 1 makes the step kernel's TMA tiles wait for bytes no copy
                                delivers, so its bounded wait expires (about 1 s per block) and
                                tslb_sums returns TSLB_ERR_TIMEOUT; 0 = off (default) */
+    int32_t plain_stores;   /* FP32 storage, blocks of 8 or 12 warps: 1 = the step kernel writes each
+                               finished plane with plain stores instead of staging it in shared
+                               memory for one TMA store; the smaller shared-memory footprint leaves
+                               the L1 cache more room, which tiles at periodic faces use (their
+                               ghost sources lie outside a tensor box, so they load element by
+                               element); 0 = staged TMA stores (default).  Results are the same
+                               either way; tslb_autotune tries both. */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
                                (blocking, so ordered with the legacy default stream) */
 } tslb_options;
@@ -239,15 +246,17 @@ TSLB_API tslb_status tslb_get_averages(tslb_ctx* ctx, int32_t instance, double* 
 TSLB_API tslb_status tslb_reset_averages(tslb_ctx* ctx);
 
 /* Tile-shape autotuner: times the step kernel for blocks of 8 and 12 warps
- * (and 16 for one grid under the projection closure) and z slabs of 16, 24,
- * 32, 48 and 64 planes, plus, for one grid, the slab depths whose block count
- * fills 2 to 8 waves of one block per SM to at least 90 % (steps_per_trial
- * launches each, CUDA events on the context stream), and keeps the fastest
- * for all later steps.  Every trial recomputes the step from the current state into
- * the spare buffer, so the state and the step index do not change.  Drops
- * captured graphs; synchronises.  Reports the choice in *block_warps and
- * *tile_z (either may be NULL). */
-TSLB_API tslb_status tslb_autotune(tslb_ctx* ctx, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z);
+ * (and 16 for one grid under the projection closure; with FP32 storage under
+ * the projection closure also the 8- and 12-warp forms with plain_stores) and
+ * z slabs of 16, 24, 32, 48 and 64 planes, plus, for one grid, the slab
+ * depths whose block count fills 2 to 8 waves of one block per SM to at least
+ * 90 % (steps_per_trial launches each, CUDA events on the context stream), and
+ * keeps the fastest for all later steps.  Every trial recomputes the step from
+ * the current state into the spare buffer, so the state and the step index do
+ * not change.  Drops captured graphs; synchronises.  Reports the choice in
+ * *block_warps, *tile_z and *plain_stores (any may be NULL). */
+TSLB_API tslb_status tslb_autotune(tslb_ctx* ctx, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z,
+                                   int32_t* plain_stores);
 
 /* The paper has no counterpart to this entry point; it serves callers that
  * must not allocate device memory when they ask for the totals.  cudaMalloc

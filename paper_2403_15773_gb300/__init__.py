@@ -64,7 +64,8 @@ class Options(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("tile_z", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("block_warps", ctypes.c_int32),
                 ("scheme", ctypes.c_int32), ("average", ctypes.c_int32), ("closure", ctypes.c_int32),
-                ("test_tma_stall", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("test_tma_stall", ctypes.c_int32), ("plain_stores", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class TslbError(RuntimeError):
@@ -125,7 +126,7 @@ def lib() -> ctypes.CDLL:
             L.tslb_batch_sums.argtypes = [VP, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double)]
             L.tslb_batch_count.argtypes = [VP]
             L.tslb_batch_count.restype = ctypes.c_int32
-            L.tslb_autotune.argtypes = [VP, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]
+            L.tslb_autotune.argtypes = [VP, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]
             L.tslb_get_averages.argtypes = [VP, ctypes.c_int32, VP, VP, P(ctypes.c_int64), ctypes.c_int]
             L.tslb_get_averages.restype = ctypes.c_int
             L.tslb_reset_averages.argtypes = [VP]
@@ -280,9 +281,11 @@ def tslb_batch_count(ctx: int) -> int:
 
 
 def tslb_autotune(ctx: int, steps_per_trial: int = 8):
-    nw, tz = ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().tslb_autotune(ctx, int(steps_per_trial), ctypes.byref(nw), ctypes.byref(tz)), ctx)
-    return nw.value, tz.value
+    """Returns the chosen (block_warps, tile_z, plain_stores)."""
+    nw, tz, pl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().tslb_autotune(ctx, int(steps_per_trial), ctypes.byref(nw), ctypes.byref(tz), ctypes.byref(pl)),
+           ctx)
+    return nw.value, tz.value, pl.value
 
 
 def tslb_get_averages(ctx: int, i: int, phi_sum: int, uz_sum: int, on_device: int) -> int:
@@ -323,7 +326,7 @@ class Simulation:
     def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
                  graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0,
                  average: bool = False, scheme: str = "fused", closure: str = "projection",
-                 test_tma_stall: bool = False):
+                 test_tma_stall: bool = False, plain_stores: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Simulation needs a CUDA device")
@@ -343,6 +346,7 @@ class Simulation:
         o.scheme = {"fused": 0, "two_sweep": 1}[scheme]
         o.closure = CLOSURES[closure]
         o.test_tma_stall = 1 if test_tma_stall else 0
+        o.plain_stores = 1 if plain_stores else 0
         self.closure = closure
         if field_scale is not None:
             for g in range(4):
@@ -450,7 +454,8 @@ class Simulation:
         tslb_synchronize(self.ctx)
 
     def autotune(self, steps_per_trial: int = 8):
-        """Pick the fastest block shape and slab depth; the state is unchanged."""
+        """Pick the fastest kernel form (block size, store path) and slab depth;
+        the state is unchanged.  Returns (block_warps, tile_z, plain_stores)."""
         return tslb_autotune(self.ctx, steps_per_trial)
 
     def averages(self):
@@ -484,7 +489,8 @@ class BatchSimulation:
     """Many independent grids (a list of :class:`inputs.Workload`) advanced
     together: one persistent launch per time step, graph-replayed."""
 
-    def __init__(self, workloads, stream=None, tile_z: int = 0, block_warps: int = 0, graph_steps: int = 0):
+    def __init__(self, workloads, stream=None, tile_z: int = 0, block_warps: int = 0, graph_steps: int = 0,
+                 plain_stores: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("BatchSimulation needs a CUDA device")
@@ -501,6 +507,7 @@ class BatchSimulation:
         o.tile_z = int(tile_z)
         o.block_warps = int(block_warps)
         o.graph_steps = int(graph_steps)
+        o.plain_stores = 1 if plain_stores else 0
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
         self.options = o
         nbytes = tslb_batch_workspace_bytes(self.grids, o)

@@ -45,6 +45,7 @@ struct tslb_ctx {
     std::vector<Instance> inst;
     bool batch = false;
     int batch_nw = 8;
+    bool batch_plain = false;
     float* staging = nullptr;
     double* partials = nullptr;   // step partials; state-sum partials after max_tiles
     int max_tiles = 0;
@@ -195,6 +196,10 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
         why = "the Chapman-Enskog closure runs blocks of 8 or 12 warps";
         return false;
     }
+    if (opt->plain_stores != 0 && opt->plain_stores != 1) {
+        why = "plain_stores must be 0 or 1";
+        return false;
+    }
     if (b.face[4] == TSLB_BC_INLET && !(b.inlet_diameter >= 0.f)) {
         why = "inlet_diameter must be >= 0";
         return false;
@@ -207,6 +212,7 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     p.block_warps = opt->block_warps > 0 ? opt->block_warps : 12;
     p.closure = opt->closure;
     p.test_stall = opt->test_tma_stall ? 1 : 0;
+    p.plain_stores = opt->plain_stores;
     p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz)
                                : auto_tile_z(grid, p.block_warps, default_tile_width(opt), device_sms());
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
@@ -356,6 +362,7 @@ tslb_status upload_batch(tslb_ctx* c) {
     for (size_t i = 0; i < c->inst.size(); ++i) {
         Instance& I = c->inst[i];
         I.p.block_warps = c->batch_nw;
+        I.p.plain_stores = c->batch_plain ? 1 : 0;
         const tslb::LaunchShape sh = tslb::step_shape(I.p, c->storage);
         I.tile_begin = (int)tiles.size();
         for (unsigned bz = 0; bz < sh.grid.z; ++bz)
@@ -401,8 +408,20 @@ cudaError_t launch_one(tslb_ctx* c, int q) {
         return tslb::launch_step(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
                                  c->partials, c->stream, &m);
     }
-    return tslb::launch_batch_step(c->batch_nw, c->dinst, c->dtiles, c->ntiles, q, c->tdev + q, c->tdev + (q ^ 1),
-                                   c->counters, c->partials, c->sms, c->stream);
+    return tslb::launch_batch_step(c->batch_nw, c->batch_plain, c->dinst, c->dtiles, c->ntiles, q, c->tdev + q,
+                                   c->tdev + (q ^ 1), c->counters, c->partials, c->sms, c->stream);
+}
+
+// One autotuner trial launch: the step from parity q again.  A batch launch
+// takes its tiles from the tile counter of its parity and only rearms the
+// other one (for the next step), so a repeated launch of the same parity
+// first resets its own.
+cudaError_t trial_launch(tslb_ctx* c, int q) {
+    if (c->batch) {
+        const cudaError_t e = cudaMemsetAsync(c->counters + q, 0, sizeof(int), c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_one(c, q);
 }
 
 void drop_graphs(tslb_ctx* c) {
@@ -534,6 +553,7 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
     c->elem = elem_size(o.storage);
     c->batch = batch;
     c->batch_nw = o.block_warps > 0 ? o.block_warps : 8;
+    c->batch_plain = o.plain_stores != 0;
     c->check_every = o.check_every > 0 ? o.check_every : 0;
     int gs = o.graph_steps > 0 ? o.graph_steps : 16;
     c->graph_steps = gs >= 2 ? gs & ~1 : 1;
@@ -891,17 +911,28 @@ std::vector<int> slab_candidates(const tslb_ctx* c, int nw) {
     return tz;
 }
 
-tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z) {
+tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z,
+                          int32_t* plain_stores) {
     if (!c) return TSLB_ERR_INVALID_ARG;
     if (steps_per_trial < 1) return bad(c, "steps_per_trial must be >= 1");
     if (!all_set(c)) return bad(c, "tslb_autotune before the state of every grid is set", TSLB_ERR_STATE);
     if (c->scheme == 1) return bad(c, "the two-sweep scheme has no tile shape to tune");
     CK(cudaSetDevice(c->device), "set device");
     const int q = c->cur;
-    // block sizes tried (16-warp blocks of the projection step for single grids only)
+    // kernel forms tried: blocks of 8 and 12 warps (16 for one grid under the
+    // projection closure), and for FP32 storage under the projection closure
+    // the 8- and 12-warp forms with plain stores as well
     const bool ce = !c->batch && c->inst[0].p.closure == tslb::CL_CHAPMAN_ENSKOG;
-    std::vector<int> shapes = {8, 12};
-    if (!ce && !c->batch) shapes.push_back(16);
+    struct Form {
+        int nw;
+        bool plain;
+    };
+    std::vector<Form> forms = {{8, false}, {12, false}};
+    if (!ce && !c->batch) forms.push_back({16, false});
+    if (!ce && c->storage == TSLB_FP32) {
+        forms.push_back({8, true});
+        forms.push_back({12, true});
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event create");
     CK(cudaEventCreate(&e1), "event create");
@@ -911,23 +942,26 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     for (Instance& I : c->inst) I.p.avg = nullptr;
     float best = 1e30f;
     int best_nw = c->batch ? c->batch_nw : c->inst[0].p.block_warps;
+    bool best_plain = c->batch ? c->batch_plain : c->inst[0].p.plain_stores != 0;
     int best_tz = keep_tz[0];
     tslb_status st = TSLB_OK;
-    for (size_t si = 0; si < shapes.size() && st == TSLB_OK; ++si)
-        for (int tz : slab_candidates(c, shapes[si])) {
+    for (size_t si = 0; si < forms.size() && st == TSLB_OK; ++si)
+        for (int tz : slab_candidates(c, forms[si].nw)) {
             // each trial re-runs the step from the current state into the other
             // buffer, so the state itself does not advance
             for (Instance& I : c->inst) {
-                I.p.block_warps = shapes[si];
+                I.p.block_warps = forms[si].nw;
+                I.p.plain_stores = forms[si].plain ? 1 : 0;
                 I.p.tile_z = std::min(tz, I.p.nz);
             }
             if (c->batch) {
-                c->batch_nw = shapes[si];
+                c->batch_nw = forms[si].nw;
+                c->batch_plain = forms[si].plain;
                 if ((st = upload_batch(c)) != TSLB_OK) break;
             }
-            cudaError_t e = launch_one(c, q);
+            cudaError_t e = trial_launch(c, q);
             if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-            for (int k = 0; k < steps_per_trial && e == cudaSuccess; ++k) e = launch_one(c, q);
+            for (int k = 0; k < steps_per_trial && e == cudaSuccess; ++k) e = trial_launch(c, q);
             if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -938,7 +972,8 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
             }
             if (ms < best) {
                 best = ms;
-                best_nw = shapes[si];
+                best_nw = forms[si].nw;
+                best_plain = forms[si].plain;
                 best_tz = tz;
             }
         }
@@ -949,21 +984,26 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
         Instance& I = c->inst[i];
         I.p.avg = I.avg;
         I.p.block_warps = best_nw;
+        I.p.plain_stores = best_plain ? 1 : 0;
         I.p.tile_z = st == TSLB_OK ? std::min(best_tz, I.p.nz) : keep_tz[i];
     }
     if (c->batch) {
         c->batch_nw = best_nw;
+        c->batch_plain = best_plain;
         tslb_status s2 = upload_batch(c);
         if (st == TSLB_OK) st = s2;
     }
     // the trials wrote the other buffer and the other step-counter slot: restore it
+    // (and rearm the tile counter of the next batch step)
     long long tt = (long long)c->t;
     CK(cudaMemcpyAsync(c->tdev + (q ^ 1), &tt, sizeof(tt), cudaMemcpyHostToDevice, c->stream), "step counter");
+    if (c->batch) CK(cudaMemsetAsync(c->counters + q, 0, sizeof(int), c->stream), "tile counter");
     CK(cudaStreamSynchronize(c->stream), "autotune synchronise");
     drop_graphs(c);
     c->parts_valid = false;
     if (block_warps) *block_warps = best_nw;
     if (tile_z) *tile_z = best_tz;
+    if (plain_stores) *plain_stores = best_plain ? 1 : 0;
     return st;
 }
 

@@ -44,6 +44,7 @@ struct StepParams {
     double* avg;             // time sums of phi and u_z (2 blocks of fstride doubles) or null
     int* err;                // set to 1 by a kernel whose bounded wait for its tile data gave up
     int test_stall;          // testing: TMA tiles expect bytes no copy delivers (the wait expires)
+    int plain_stores;        // FP32, 8 or 12 warps: plain stores instead of the staging box + TMA store
 };
 
 // Tensor maps of one step for the TMA tile copies of the step kernel: the 10
@@ -121,9 +122,11 @@ int max_partials(const StepParams& p, int storage);
 
 // Batched FP32 step: tiles[k] = (instance, bx, by, bz) over all instances,
 // taken from counters[parity] by one persistent block per SM on `sms` SMs,
-// blocks of `nw` warps (8 or 12); tile k writes partials[2k..2k+1].
+// blocks of `nw` warps (8 or 12), with plain stores if `plain`; tile k
+// writes partials[2k..2k+1].
 cudaError_t prepare_batch_kernels();
-cudaError_t launch_batch_step(int nw, const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
+cudaError_t launch_batch_step(int nw, bool plain, const BatchInstance* insts, const int4* tiles, int ntiles,
+                              int parity,
                               const long long* t_in, long long* t_out, int* counters, double* partials,
                               int sms, cudaStream_t s);
 

@@ -49,12 +49,15 @@ namespace {
 
 // ----------------------------------------------------- step kernel (pairs)
 
-// Shared memory of a block of NW warps with storage type S.  The moment and
+// Shared memory of a block of NW warps with storage type S; ST: the staging
+// box of finished planes (FP32 blocks of up to 12 warps; without it, plain
+// stores and a smaller footprint, which leaves the L1 cache more of the
+// storage it shares with shared memory).  The moment and
 // phase-field planes of a tile are held as the boxes a TMA copy writes: a
 // moment box is [10 fields][NR rows][MW columns], a phase-field box
 // [NR + 2 rows][PW columns], each starting at the staged tile's first column
 // rounded down to 16 bytes (offsets offm / offp inside the box).
-template <int NW, typename S>
+template <int NW, typename S, bool ST = true>
 struct Step2Smem {
     static constexpr int NT = 32 * NW;                       // threads
     static constexpr int NR = 2 * NW;                        // staged rows (two per warp)
@@ -68,7 +71,7 @@ struct Step2Smem {
     static constexpr bool kFp32 = sizeof(S) == 4;
     static constexpr int TXS = TX;
     // (16-warp blocks have no room for the staging boxes: plain stores)
-    static constexpr bool kTmaStore = kFp32 && NW <= 12;
+    static constexpr bool kTmaStore = kFp32 && NW <= 12 && ST;
     // box columns: staged columns x0-1 .. x0+30 (moments) and x0-2 .. x0+31
     // (phase field) from the 16-byte boundary below them
     static constexpr int MW = kFp32 ? 36 : 40;
@@ -111,11 +114,11 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 // (bx, by), planes [bz * tile_z, (bz + 1) * tile_z), from state `in` (step t)
 // to state `out`; writes the tile's FP64 partial sums to part[0..1].
 // maps: tensor maps of `in` for TMA loads, or null (element-wise loads).
-template <int NW, typename S>
+template <int NW, typename S, bool ST>
 __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
                                           S* __restrict__ out, const long long t, const int bx, const int by,
                                           const int bz, double* __restrict__ part) {
-    using L = Step2Smem<NW, S>;
+    using L = Step2Smem<NW, S, ST>;
     constexpr int NT = L::NT, NR = L::NR, NPH = L::NPH, MW = L::MW, PW = L::PW, FS = L::FS, AL = L::AL;
     constexpr int TY = L::TY;
     constexpr int OSL = (int)(L::OUT_SLOT / sizeof(float));
@@ -664,14 +667,14 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
 }
 
 // One time step of one grid: one block per tile.
-template <int NW, typename S>
+template <int NW, typename S, bool ST>
 __global__ void __launch_bounds__(32 * NW, 1)
     step2_kernel(const __grid_constant__ StepParams P, const __grid_constant__ TileMaps M, const S* __restrict__ in,
                  S* __restrict__ out, const long long* __restrict__ t_in, long long* __restrict__ t_out,
                  double* __restrict__ partials) {
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const long long t = *t_in;
-    step_tile<NW, S>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+    step_tile<NW, S, ST>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
     if (blk == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_out = t + 1;
 }
 
@@ -681,7 +684,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
 // instance's parameters are staged in shared memory for the tile; its tensor
 // maps are read from the instance table in device memory.  counters[q]
 // serves the steps of parity q; each launch zeroes the other one for the next.
-template <int NW>
+template <int NW, bool ST>
 __global__ void __launch_bounds__(32 * NW, 1)
     step_batch_kernel(const BatchInstance* __restrict__ insts, const int4* __restrict__ tiles, int ntiles,
                       int parity, const long long* __restrict__ t_in, long long* __restrict__ t_out,
@@ -711,8 +714,8 @@ __global__ void __launch_bounds__(32 * NW, 1)
         // the grid's tensor maps live in device memory, written before the launch
         const TileMaps* maps = &insts[tl.x].maps[parity];
         if (tid == 0) fence_tensormap_acquire(maps);
-        step_tile<NW, float>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
-                             partials + 2 * k);
+        step_tile<NW, float, ST>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
+                                 partials + 2 * k);
     }
     if (blockIdx.x == 0 && tid == 0) *t_out = t + 1;
 }
@@ -820,7 +823,7 @@ int conv_blocks(const StepParams& p) {
     return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
 }
 
-template <int NW, typename S>
+template <int NW, typename S, bool ST>
 cudaError_t launch_nw(const StepParams& p, int storage, const void* in, void* out, const long long* t_in,
                       long long* t_out, double* partials, cudaStream_t s, const TileMaps* maps) {
     const LaunchShape sh = step_shape(p, storage);
@@ -829,49 +832,58 @@ cudaError_t launch_nw(const StepParams& p, int storage, const void* in, void* ou
         memset(&none, 0, sizeof(none));
         maps = &none;
     }
-    step2_kernel<NW, S><<<sh.grid, sh.block, sh.smem, s>>>(p, *maps, static_cast<const S*>(in),
-                                                           static_cast<S*>(out), t_in, t_out, partials);
+    step2_kernel<NW, S, ST><<<sh.grid, sh.block, sh.smem, s>>>(p, *maps, static_cast<const S*>(in),
+                                                               static_cast<S*>(out), t_in, t_out, partials);
     return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_step_t(const StepParams& p, int st, const void* in, void* out, const long long* t_in,
                           long long* t_out, double* partials, cudaStream_t s, const TileMaps* m) {
+    if constexpr (sizeof(S) == 4) {  // FP32 blocks of 8 or 12 warps without the staging box
+        if (p.plain_stores && p.block_warps == 8) return launch_nw<8, S, false>(p, st, in, out, t_in, t_out, partials, s, m);
+        if (p.plain_stores && p.block_warps == 12)
+            return launch_nw<12, S, false>(p, st, in, out, t_in, t_out, partials, s, m);
+    }
     switch (p.block_warps) {
-        case 8: return launch_nw<8, S>(p, st, in, out, t_in, t_out, partials, s, m);
-        case 12: return launch_nw<12, S>(p, st, in, out, t_in, t_out, partials, s, m);
-        case 16: return launch_nw<16, S>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 8: return launch_nw<8, S, true>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 12: return launch_nw<12, S, true>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 16: return launch_nw<16, S, true>(p, st, in, out, t_in, t_out, partials, s, m);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int NW, typename S>
+template <int NW, typename S, bool ST>
 cudaError_t prepare_nw() {
-    return cudaFuncSetAttribute(step2_kernel<NW, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Step2Smem<NW, S>::BYTES);
+    return cudaFuncSetAttribute(step2_kernel<NW, S, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Step2Smem<NW, S, ST>::BYTES);
 }
 
-template <int NW>
+template <int NW, bool ST>
 cudaError_t launch_batch_nw(const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
                             const long long* t_in, long long* t_out, int* counters, double* partials, int sms,
                             cudaStream_t s) {
-    step_batch_kernel<NW><<<sms, dim3(32, NW, 1), Step2Smem<NW, float>::BYTES, s>>>(
+    step_batch_kernel<NW, ST><<<sms, dim3(32, NW, 1), Step2Smem<NW, float, ST>::BYTES, s>>>(
         insts, tiles, ntiles, parity, t_in, t_out, counters, partials);
     return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t prepare_t() {
-    cudaError_t e = prepare_nw<8, S>();
-    if (e == cudaSuccess) e = prepare_nw<12, S>();
-    if (e == cudaSuccess) e = prepare_nw<16, S>();
+    cudaError_t e = prepare_nw<8, S, true>();
+    if (e == cudaSuccess) e = prepare_nw<12, S, true>();
+    if (e == cudaSuccess) e = prepare_nw<16, S, true>();
+    if constexpr (sizeof(S) == 4) {
+        if (e == cudaSuccess) e = prepare_nw<8, S, false>();
+        if (e == cudaSuccess) e = prepare_nw<12, S, false>();
+    }
     return e;
 }
 
-template <int NW>
+template <int NW, bool ST>
 cudaError_t prepare_batch_nw() {
-    return cudaFuncSetAttribute(step_batch_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Step2Smem<NW, float>::BYTES);
+    return cudaFuncSetAttribute(step_batch_kernel<NW, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Step2Smem<NW, float, ST>::BYTES);
 }
 
 }  // namespace
@@ -879,17 +891,23 @@ cudaError_t prepare_batch_nw() {
 static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied as ints");
 
 cudaError_t prepare_batch_kernels() {
-    cudaError_t e = prepare_batch_nw<8>();
-    if (e == cudaSuccess) e = prepare_batch_nw<12>();
+    cudaError_t e = prepare_batch_nw<8, true>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12, true>();
+    if (e == cudaSuccess) e = prepare_batch_nw<8, false>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12, false>();
     return e;
 }
 
-cudaError_t launch_batch_step(int nw, const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
-                              const long long* t_in, long long* t_out, int* counters, double* partials,
-                              int sms, cudaStream_t s) {
-    switch (nw) {
-        case 8: return launch_batch_nw<8>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
-        case 12: return launch_batch_nw<12>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
+cudaError_t launch_batch_step(int nw, bool plain, const BatchInstance* insts, const int4* tiles, int ntiles,
+                              int parity, const long long* t_in, long long* t_out, int* counters,
+                              double* partials, int sms, cudaStream_t s) {
+    const int key = nw * 2 + (plain ? 1 : 0);
+    switch (key) {
+        case 16: return launch_batch_nw<8, true>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
+        case 17: return launch_batch_nw<8, false>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
+        case 24: return launch_batch_nw<12, true>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
+        case 25:
+            return launch_batch_nw<12, false>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -904,7 +922,9 @@ cudaError_t prepare_kernels(int storage) {
 }
 
 template <typename S>
-size_t step_smem_bytes_t(int nw) {
+size_t step_smem_bytes_t(int nw, bool plain) {
+    if (sizeof(S) == 4 && plain && nw == 8) return Step2Smem<8, S, false>::BYTES;
+    if (sizeof(S) == 4 && plain && nw == 12) return Step2Smem<12, S, false>::BYTES;
     switch (nw) {
         case 8: return Step2Smem<8, S>::BYTES;
         case 12: return Step2Smem<12, S>::BYTES;
@@ -912,8 +932,8 @@ size_t step_smem_bytes_t(int nw) {
     }
 }
 
-size_t step_smem_bytes(int nw, int storage) {
-    return storage == ST_FP32 ? step_smem_bytes_t<float>(nw) : step_smem_bytes_t<__half>(nw);
+size_t step_smem_bytes(int nw, int storage, bool plain) {
+    return storage == ST_FP32 ? step_smem_bytes_t<float>(nw, plain) : step_smem_bytes_t<__half>(nw, plain);
 }
 
 LaunchShape step_shape(const StepParams& p, int storage) {
@@ -923,7 +943,7 @@ LaunchShape step_shape(const StepParams& p, int storage) {
     const int tx = TX;  // 28 interior columns for every kernel
     sh.grid = dim3((p.nx + tx - 1) / tx, (p.ny + ty - 1) / ty, (p.nz + p.tile_z - 1) / p.tile_z);
     sh.block = dim3(32, sh.nw, 1);
-    sh.smem = step_smem_bytes(sh.nw, storage);
+    sh.smem = step_smem_bytes(sh.nw, storage, p.plain_stores != 0);
     return sh;
 }
 

@@ -38,10 +38,11 @@ def single_run(w, steps, **kw):
     return out, sums
 
 
-@pytest.mark.parametrize("block_warps,tile_z", [(8, 16), (12, 32), (8, 0)])
-def test_batch_equals_each_grid_alone(block_warps, tile_z):
+@pytest.mark.parametrize("block_warps,tile_z,plain", [(8, 16, False), (12, 32, False), (8, 0, False),
+                                                     (12, 24, True), (8, 40, True)])
+def test_batch_equals_each_grid_alone(block_warps, tile_z, plain):
     ws = small_ensemble()
-    b = tslb.BatchSimulation(ws, block_warps=block_warps, tile_z=tile_z)
+    b = tslb.BatchSimulation(ws, block_warps=block_warps, tile_z=tile_z, plain_stores=plain)
     for i, w in enumerate(ws):
         rho, u, phi = w.fields()
         b.set_state(i, rho, u, phi)
@@ -86,8 +87,8 @@ def test_autotune_does_not_change_the_trajectory():
     rho, u, phi = w.fields()
     s.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
     s.step(5)
-    nw, tz = s.autotune(4)
-    assert nw in (8, 12) and tz in (16, 24, 32, 48, 64)
+    nw, tz, plain = s.autotune(4)
+    assert nw in (8, 12, 16) and 8 <= tz <= 128 and plain in (0, 1)
     assert s.t == 5
     s.step(20)
     got = s.fields_numpy()
@@ -111,5 +112,29 @@ def test_batch_autotune_keeps_state():
         ga, gb = a.fields_numpy(i), b.fields_numpy(i)
         for k in range(4):
             assert np.array_equal(ga[k], gb[k])
+    a.close()
+    b.close()
+
+
+def test_batch_step_after_autotune_runs_every_tile():
+    """The autotuner re-runs the same step many times; afterwards the next
+    step must again take every tile (its tile counter rearmed): a new state
+    set after tuning is stepped, not left at the trials' result."""
+    ws = small_ensemble()[:3]
+    new = [inputs.random_smooth_fields(w.nx, w.ny, w.nz, seed=40 + i, amp_rho=1e-3, amp_u=1e-2)
+           for i, w in enumerate(ws)]
+    a = tslb.BatchSimulation(ws)
+    for i, w in enumerate(ws):
+        a.set_state(i, *w.fields())
+    a.autotune(2)
+    b = tslb.BatchSimulation(ws)
+    for sim in (a, b):
+        for i, (rho, u, _, _) in enumerate(new):
+            sim.set_state(i, rho, u, ws[i].fields()[2])
+        sim.step(1)
+    for i in range(len(ws)):
+        ga, gb = a.fields_numpy(i), b.fields_numpy(i)
+        for k in range(4):
+            assert np.array_equal(ga[k], gb[k]), (i, k)
     a.close()
     b.close()
