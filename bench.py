@@ -39,10 +39,15 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_2403_15773_gb300", "csrc", f)
 
 
 def kernel_source_sha() -> str:
+    """Hash of the step kernel's code (comments and whitespace removed, so that
+    a comment edit does not orphan the ncu summary taken on the same code)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -3,9 +3,9 @@
 //
 // One launch = one time step over the whole grid.  Each thread block owns a
 // slab of 28 x TY interior columns and marches through its z range plane by
-// plane.  A warp holds two
-// rows of 32 staged columns (interior + halo); the block holds TY interior
-// rows plus one halo row above and below.
+// plane.  A warp holds two rows of 32 staged columns (interior, one halo
+// column each side, two spare lanes); the block holds TY interior rows plus
+// one halo row above and below.
 //
 // Per staged node and plane the kernel
 //   1. reads the moments (rho - 1, u, P) and the phase field of the node and of
@@ -34,9 +34,10 @@
 //      rho' = sum_i f_i(x - c_i), j' = sum_i c_i f_i(x - c_i),
 //      Pi' = sum_i c_i c_i f_i(x - c_i) up to FP32 rounding;
 //   5. stores rho' - 1, u' = j'/rho', P' = Pi' - rho' cs2 I - rho' u' u' and
-//      phi' (FP32: into a staging box that leaves by one TMA store per plane;
-//      16-bit: plain stores), and accumulates the FP64 block partials of
-//      sum(rho - 1), sum(phi).
+//      phi' (FP32: into a staging box that leaves by one TMA store per plane,
+//      or with plain stores in the kernel form without the box; 16-bit: plain
+//      stores), and accumulates the FP64 block partials of sum(rho - 1),
+//      sum(phi).
 //
 // All arithmetic is FP32 and works with deviations from the rest state
 // (rho - 1, Pi - cs2 I) so that no O(1) terms cancel.
