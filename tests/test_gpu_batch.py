@@ -138,3 +138,25 @@ def test_batch_step_after_autotune_runs_every_tile():
             assert np.array_equal(ga[k], gb[k]), (i, k)
     a.close()
     b.close()
+
+
+def test_full_ensemble_in_the_benchmark_configuration():
+    """The 64-grid ensemble of the benchmark, autotuned as bench.py does: after
+    three steps its smallest grid, a jet and its largest grid equal the same
+    grids run alone, bit for bit."""
+    ws = inputs.batched_ensemble()
+    b = tslb.BatchSimulation(ws)
+    for i, w in enumerate(ws):
+        b.set_state(i, *w.fields())
+    nw, tz, plain = b.autotune(3)
+    assert nw in (8, 12) and plain in (0, 1)
+    b.step(3)
+    sizes = [w.nodes for w in ws]
+    jets = [i for i, w in enumerate(ws) if w.kind == "jet"]
+    picks = {int(np.argmin(sizes)), int(np.argmax(sizes)), jets[0]}
+    for i in sorted(picks):
+        got = b.fields_numpy(i)
+        ref, _ = single_run(ws[i], 3)
+        for k in range(4):
+            assert np.array_equal(got[k], ref[k]), (i, k)
+    b.close()
