@@ -46,6 +46,7 @@ struct tslb_ctx {
     bool batch = false;
     int batch_nw = 8;
     bool batch_plain = false;
+    bool batch_wrap = false;  // some instance has the side-box maps of periodic faces
     float* staging = nullptr;
     double* partials = nullptr;   // step partials; state-sum partials after max_tiles
     int max_tiles = 0;
@@ -375,6 +376,8 @@ tslb_status upload_batch(tslb_ctx* c) {
         for (int q = 0; q < 2; ++q)
             CK(tslb::make_tile_maps(I.p, c->storage, I.buf[q], I.buf[q ^ 1], &di[i].maps[q]), "batch tensor maps");
     }
+    c->batch_wrap = false;
+    for (const tslb::BatchInstance& b : di) c->batch_wrap = c->batch_wrap || (b.maps[0].wrap && b.maps[1].wrap);
     if ((int)tiles.size() > c->max_tiles) return bad(c, "batch tile list exceeds its workspace");
     c->ntiles = (int)tiles.size();
     CK(cudaMemcpyAsync(c->dinst, di.data(), di.size() * sizeof(di[0]), cudaMemcpyHostToDevice, c->stream),
@@ -408,8 +411,8 @@ cudaError_t launch_one(tslb_ctx* c, int q) {
         return tslb::launch_step(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
                                  c->partials, c->stream, &m);
     }
-    return tslb::launch_batch_step(c->batch_nw, c->batch_plain, c->dinst, c->dtiles, c->ntiles, q, c->tdev + q,
-                                   c->tdev + (q ^ 1), c->counters, c->partials, c->sms, c->stream);
+    return tslb::launch_batch_step(c->batch_nw, c->batch_plain, c->batch_wrap, c->dinst, c->dtiles, c->ntiles, q,
+                                   c->tdev + q, c->tdev + (q ^ 1), c->counters, c->partials, c->sms, c->stream);
 }
 
 // One autotuner trial launch: the step from parity q again.  A batch launch

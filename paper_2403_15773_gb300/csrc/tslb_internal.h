@@ -52,12 +52,19 @@ struct StepParams {
 // phase field as a 3D tensor {nx, ny, nz}, and (FP32) the 11 fields of the
 // output buffer, with the box shapes of the block size they were made for.
 // valid = 0: every tile loads element by element; store = 0: plain stores.
+// FP32 grids with periodic x or y faces also get the side boxes that bring a
+// tile the sources of its ghosts across those faces (wrap = 1): a 4-column
+// strip of the moments (x wrap), one moment row (y wrap) and their 4-column
+// corner, and the phase-field equivalents (two rows).
 struct TileMaps {
     CUtensorMap mom;
     CUtensorMap phi;
     CUtensorMap out;
+    CUtensorMap momx, momy, momc;
+    CUtensorMap phix, phiy, phic;
     int valid;
     int store;
+    int wrap;
     int block_warps;
 };
 
@@ -122,13 +129,13 @@ int max_partials(const StepParams& p, int storage);
 
 // Batched FP32 step: tiles[k] = (instance, bx, by, bz) over all instances,
 // taken from counters[parity] by one persistent block per SM on `sms` SMs,
-// blocks of `nw` warps (8 or 12), with plain stores if `plain`; tile k
+// blocks of `nw` warps (8 or 12), with plain stores if `plain`, in the form
+// for periodic faces if `wrap` (some instance has side-box maps); tile k
 // writes partials[2k..2k+1].
 cudaError_t prepare_batch_kernels();
-cudaError_t launch_batch_step(int nw, bool plain, const BatchInstance* insts, const int4* tiles, int ntiles,
-                              int parity,
-                              const long long* t_in, long long* t_out, int* counters, double* partials,
-                              int sms, cudaStream_t s);
+cudaError_t launch_batch_step(int nw, bool plain, bool wrap, const BatchInstance* insts, const int4* tiles,
+                              int ntiles, int parity, const long long* t_in, long long* t_out, int* counters,
+                              double* partials, int sms, cudaStream_t s);
 
 // The paper's two-sweep design (ablation): collide+push of the moments M into
 // 34 population arrays `pops` (27 f_i - w_i, then 7 g_k), then the moments of

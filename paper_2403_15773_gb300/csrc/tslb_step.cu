@@ -58,7 +58,7 @@ namespace {
 // moment box is [10 fields][NR rows][MW columns], a phase-field box
 // [NR + 2 rows][PW columns], each starting at the staged tile's first column
 // rounded down to 16 bytes (offsets offm / offp inside the box).
-template <int NW, typename S, bool ST = true>
+template <int NW, typename S, bool ST = true, bool WR = false>
 struct Step2Smem {
     static constexpr int NT = 32 * NW;                       // threads
     static constexpr int NR = 2 * NW;                        // staged rows (two per warp)
@@ -82,7 +82,17 @@ struct Step2Smem {
     static constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t MOM_BOX = sizeof(S) * 10 * FS;           // bytes of one moment box
     static constexpr size_t PHI_BOX = sizeof(S) * (NR + 2) * PW;     // bytes of one phase-field box
-    static constexpr size_t MOM_SLOT = r128(MOM_BOX), PHI_SLOT = r128(PHI_BOX);
+    // WR: each slot also holds the side boxes of ghosts across periodic faces,
+    // after its box: moments X [10][NR][4], Y [10][MW], C [10][4]; phase field
+    // X [NR + 2][4], Y [2][PW], C [2][4] (byte offsets within the slot)
+    static constexpr size_t MX_BYTES = sizeof(S) * 10 * NR * 4, MY_BYTES = sizeof(S) * 10 * MW;
+    static constexpr size_t MC_BYTES = sizeof(S) * 10 * 4;
+    static constexpr size_t PX_BYTES = sizeof(S) * (NR + 2) * 4, PY_BYTES = sizeof(S) * 2 * PW;
+    static constexpr size_t PC_BYTES = sizeof(S) * 2 * 4;
+    static constexpr size_t MX = r128(MOM_BOX), MY = MX + r128(MX_BYTES), MC = MY + r128(MY_BYTES);
+    static constexpr size_t PX = r128(PHI_BOX), PY = PX + r128(PX_BYTES), PC = PY + r128(PY_BYTES);
+    static constexpr size_t MOM_SLOT = WR ? MC + r128(MC_BYTES) : r128(MOM_BOX);
+    static constexpr size_t PHI_SLOT = WR ? PC + r128(PC_BYTES) : r128(PHI_BOX);
     // planes between the load of a plane's moments and their use (the phase
     // field is loaded two planes further ahead); 16 warps: shared memory
     // holds one plane less
@@ -115,11 +125,11 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 // (bx, by), planes [bz * tile_z, (bz + 1) * tile_z), from state `in` (step t)
 // to state `out`; writes the tile's FP64 partial sums to part[0..1].
 // maps: tensor maps of `in` for TMA loads, or null (element-wise loads).
-template <int NW, typename S, bool ST>
+template <int NW, typename S, bool ST, bool WR>
 __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
                                           S* __restrict__ out, const long long t, const int bx, const int by,
                                           const int bz, double* __restrict__ part) {
-    using L = Step2Smem<NW, S, ST>;
+    using L = Step2Smem<NW, S, ST, WR>;
     constexpr int NT = L::NT, NR = L::NR, NPH = L::NPH, MW = L::MW, PW = L::PW, FS = L::FS, AL = L::AL;
     constexpr int TY = L::TY;
     constexpr int OSL = (int)(L::OUT_SLOT / sizeof(float));
@@ -183,6 +193,52 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     const int resA = useA ? (syA - ym) * MW + (sx - xm) : mrdA, resB = useB ? (syB - ym) * MW + (sx - xm) : mrdB;
     bool inbox = (!useA || (sx >= xm && sx - xm < MW && syA >= ym && syA - ym < NR)) &&
                  (!useB || (sx >= xm && sx - xm < MW && syB >= ym && syB - ym < NR));
+    // WR kernels (FP32 grids with periodic x or y faces): a ghost across such a
+    // face reads its source from the side boxes loaded with the plane (a
+    // 4-column strip at x = nx - 4 or 0, one moment row / two phase-field rows
+    // at y = ny - 1 (ny - 2) or 0, their corner), at its own field stride.  A
+    // tile needs at most one x strip and one y strip (else it loads element
+    // by element).
+    int fsA = FS, fsB = FS;
+    bool wrx = false, wry = false;
+    int xs0 = 0, ysm = 0, ysp = 0;
+    [[maybe_unused]] const bool perx = P.face[0] == BC_PERIODIC, pery = P.face[2] == BC_PERIODIC;
+    if constexpr (WR) {
+        const bool xl = perx && x0 == 0, xr = perx && x0 + 31 >= nx;
+        const bool yt = pery && y0 == 0, yb = pery && y0 + NR - 1 >= ny;
+        wrx = xl || xr;
+        wry = yt || yb;
+        xs0 = xl ? nx - 4 : 0;
+        ysm = yt ? ny - 1 : 0;
+        ysp = yt ? ny - 2 : 0;
+        bool ok = !(xl && xr) && !(yt && yb);
+        auto side = [&](bool use, int gy, int sy, int& rd, int& fsd, int res) {
+            if (!use) return;
+            const bool wx = perx && (gx < 0 || gx >= nx), wy = pery && (gy < 0 || gy >= ny);
+            if (!wx && !wy) {
+                rd = res;
+                ok = ok && sx >= xm && sx - xm < MW && sy >= ym && sy - ym < NR;
+            } else if (!wy) {
+                rd = (int)(L::MX / sizeof(S)) + (sy - ym) * 4 + (sx - xs0);
+                fsd = NR * 4;
+                ok = ok && sy >= ym && sy - ym < NR && sx >= xs0 && sx - xs0 < 4;
+            } else if (!wx) {
+                rd = (int)(L::MY / sizeof(S)) + (sx - xm);
+                fsd = MW;
+                ok = ok && sx >= xm && sx - xm < MW && sy == ysm;
+            } else {
+                rd = (int)(L::MC / sizeof(S)) + (sx - xs0);
+                fsd = 4;
+                ok = ok && sx >= xs0 && sx - xs0 < 4 && sy == ysm;
+            }
+        };
+        int rA = mrdA, rB = mrdB;
+        side(useA, gyA, syA, rA, fsA, resA);
+        side(useB, gyB, syB, rB, fsB, resB);
+        inbox = ok;
+        mrdA = rA;
+        mrdB = rB;
+    }
     int pxy[EPT], prd[EPT], pres[EPT];
     float phib[EPT];
     const bool inlet_face = P.face[4] == BC_INLET;
@@ -203,16 +259,37 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
             pxy[e] = psx + nx * psy;
             prd[e] = r * PW + c + offp;
             pres[e] = used ? (psy - yp) * PW + (psx - xp) : prd[e];
-            inbox = inbox && (!used || (psx >= xp && psx - xp < PW && psy >= yp && psy - yp < NR + 2));
+            const bool wxe = WR && perx && (gxe < 0 || gxe >= nx), wye = WR && pery && (gye < 0 || gye >= ny);
+            if (used && (wxe || wye)) {  // WR: phase-field side boxes
+                const int px0 = (int)(L::PX / sizeof(S)), py0 = (int)(L::PY / sizeof(S)), pc0 = (int)(L::PC / sizeof(S));
+                if (!wye) {
+                    pres[e] = px0 + (psy - yp) * 4 + (psx - xs0);
+                    inbox = inbox && psy >= yp && psy - yp < NR + 2 && psx >= xs0 && psx - xs0 < 4;
+                } else if (!wxe) {
+                    pres[e] = py0 + (psy - ysp) * PW + (psx - xp);
+                    inbox = inbox && psy >= ysp && psy - ysp < 2 && psx >= xp && psx - xp < PW;
+                } else {
+                    pres[e] = pc0 + (psy - ysp) * 4 + (psx - xs0);
+                    inbox = inbox && psy >= ysp && psy - ysp < 2 && psx >= xs0 && psx - xs0 < 4;
+                }
+            } else {
+                inbox = inbox && (!used || (psx >= xp && psx - xp < PW && psy >= yp && psy - yp < NR + 2));
+            }
             if (inlet_planes) phib[e] = inlet_phi(P, psx, psy);
         }
     }
-    const bool tma = __syncthreads_and(use_maps && inbox) != 0;
+    const bool tma = __syncthreads_and(use_maps && inbox && (!WR || !(wrx || wry) || maps->wrap)) != 0;
     if (tma) {
-        mrdA = resA;
-        mrdB = resB;
+        if constexpr (!WR) {  // (WR: mrdA / mrdB set above)
+            mrdA = resA;
+            mrdB = resB;
+        }
 #pragma unroll
         for (int e = 0; e < EPT; ++e) prd[e] = pres[e];
+    } else if constexpr (WR) {  // element-wise after all: own positions, box stride
+        mrdA = (2 * w) * MW + lane + offm;
+        mrdB = mrdA + MW;
+        fsA = fsB = FS;
     }
 
     // Loads of the phase field at plane qp (if do_p) and the moments at plane
@@ -222,6 +299,30 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     // until commit().  Inlet planes of the phase field are never loaded (the
     // imposed values are used directly).  Returns whether bar[kb] got copies.
     unsigned short rphi[EPT], rmom[2][10];
+    // bytes a plane's phase-field / moment copies deliver (WR: with the side boxes)
+    const unsigned pbytes = (unsigned)L::PHI_BOX + (WR ? (wrx ? (unsigned)L::PX_BYTES : 0u) +
+                                                             (wry ? (unsigned)L::PY_BYTES : 0u) +
+                                                             (wrx && wry ? (unsigned)L::PC_BYTES : 0u)
+                                                       : 0u);
+    const unsigned mbytes = (unsigned)L::MOM_BOX + (WR ? (wrx ? (unsigned)L::MX_BYTES : 0u) +
+                                                             (wry ? (unsigned)L::MY_BYTES : 0u) +
+                                                             (wrx && wry ? (unsigned)L::MC_BYTES : 0u)
+                                                       : 0u);
+    // WR: the side boxes of plane z (resolved) into the slots at dp / dm
+    auto side_phi = [&](S* dp, int z, uint64_t* b) {
+        if constexpr (WR) {
+            if (wrx) tma_load_3d(dp + L::PX / sizeof(S), &maps->phix, xs0, yp, z, b);
+            if (wry) tma_load_3d(dp + L::PY / sizeof(S), &maps->phiy, xp, ysp, z, b);
+            if (wrx && wry) tma_load_3d(dp + L::PC / sizeof(S), &maps->phic, xs0, ysp, z, b);
+        }
+    };
+    auto side_mom = [&](S* dm, int z, uint64_t* b) {
+        if constexpr (WR) {
+            if (wrx) tma_load_4d(dm + L::MX / sizeof(S), &maps->momx, xs0, ym, z, 0, b);
+            if (wry) tma_load_4d(dm + L::MY / sizeof(S), &maps->momy, xm, ysm, z, 0, b);
+            if (wrx && wry) tma_load_4d(dm + L::MC / sizeof(S), &maps->momc, xs0, ysm, z, 0, b);
+        }
+    };
     auto issue = [&](bool do_p, int qp, bool do_m, int qm, int kb) -> bool {
         // only the inlet face is never loaded (its phase field is imposed)
         const bool lp = do_p && !(inlet_face && qp < 0);
@@ -230,13 +331,17 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
                 float sg;
                 int in2 = 0;
                 fence_proxy_async();
-                mbar_expect_tx(bar + kb, (lp ? (unsigned)L::PHI_BOX : 0u) + (do_m ? (unsigned)L::MOM_BOX : 0u));
-                if (lp)
-                    tma_load_3d(ring + pslot(qp) * PSL, &maps->phi, xp, yp,
-                                resolve_axis(qp, nz, P.face[4], P.face[5], sg, in2), bar + kb);
-                if (do_m)
-                    tma_load_4d(momb + mslot(qm) * MSL, &maps->mom, xm, ym,
-                                resolve_axis(qm, nz, P.face[4], P.face[5], sg, in2), 0, bar + kb);
+                mbar_expect_tx(bar + kb, (lp ? pbytes : 0u) + (do_m ? mbytes : 0u));
+                if (lp) {
+                    const int z = resolve_axis(qp, nz, P.face[4], P.face[5], sg, in2);
+                    tma_load_3d(ring + pslot(qp) * PSL, &maps->phi, xp, yp, z, bar + kb);
+                    side_phi(ring + pslot(qp) * PSL, z, bar + kb);
+                }
+                if (do_m) {
+                    const int z = resolve_axis(qm, nz, P.face[4], P.face[5], sg, in2);
+                    tma_load_4d(momb + mslot(qm) * MSL, &maps->mom, xm, ym, z, 0, bar + kb);
+                    side_mom(momb + mslot(qm) * MSL, z, bar + kb);
+                }
             }
             return lp || do_m;
         }
@@ -333,19 +438,23 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         if (tid == 0) {
             float sg;
             int in2 = 0;
-            unsigned bytes = PF * (unsigned)L::MOM_BOX;
+            unsigned bytes = PF * mbytes;
             for (int q = z0 - 2; q <= z0 + PF; ++q)
-                if (!(inlet_face && q < 0)) bytes += (unsigned)L::PHI_BOX;
+                if (!(inlet_face && q < 0)) bytes += pbytes;
             fence_proxy_async();
             // (P.test_stall: 16 bytes more than the copies deliver, so the wait below expires)
             mbar_expect_tx(bar + BPRO, bytes + (P.test_stall ? 16u : 0u));
             for (int q = z0 - 2; q <= z0 + PF; ++q)
-                if (!(inlet_face && q < 0))
-                    tma_load_3d(ring + pslot(q) * PSL, &maps->phi, xp, yp,
-                                resolve_axis(q, nz, P.face[4], P.face[5], sg, in2), bar + BPRO);
-            for (int k = 0; k < PF; ++k)
-                tma_load_4d(momb + mslot(z0 - 1 + k) * MSL, &maps->mom, xm, ym,
-                            resolve_axis(z0 - 1 + k, nz, P.face[4], P.face[5], sg, in2), 0, bar + BPRO);
+                if (!(inlet_face && q < 0)) {
+                    const int z = resolve_axis(q, nz, P.face[4], P.face[5], sg, in2);
+                    tma_load_3d(ring + pslot(q) * PSL, &maps->phi, xp, yp, z, bar + BPRO);
+                    side_phi(ring + pslot(q) * PSL, z, bar + BPRO);
+                }
+            for (int k = 0; k < PF; ++k) {
+                const int z = resolve_axis(z0 - 1 + k, nz, P.face[4], P.face[5], sg, in2);
+                tma_load_4d(momb + mslot(z0 - 1 + k) * MSL, &maps->mom, xm, ym, z, 0, bar + BPRO);
+                side_mom(momb + mslot(z0 - 1 + k) * MSL, z, bar + BPRO);
+            }
         }
         pend |= 1u << BPRO;
     } else {
@@ -422,7 +531,8 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
             const S* mA = momb + mslot(i) * MSL + mrdA;
             const S* mB = momb + mslot(i) * MSL + mrdB;
             auto ld2 = [&](int f) {
-                return make_float2(Io<S>::cvt(mA[f * FS], P.inv_scale[f]), Io<S>::cvt(mB[f * FS], P.inv_scale[f]));
+                return make_float2(Io<S>::cvt(mA[f * (WR ? fsA : FS)], P.inv_scale[f]),
+                                   Io<S>::cvt(mB[f * (WR ? fsB : FS)], P.inv_scale[f]));
             };
             const float2 sgy = make_float2(sgyA, sgyB);
             const float2 drho = ld2(0);
@@ -668,14 +778,14 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
 }
 
 // One time step of one grid: one block per tile.
-template <int NW, typename S, bool ST>
+template <int NW, typename S, bool ST, bool WR>
 __global__ void __launch_bounds__(32 * NW, 1)
     step2_kernel(const __grid_constant__ StepParams P, const __grid_constant__ TileMaps M, const S* __restrict__ in,
                  S* __restrict__ out, const long long* __restrict__ t_in, long long* __restrict__ t_out,
                  double* __restrict__ partials) {
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const long long t = *t_in;
-    step_tile<NW, S, ST>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+    step_tile<NW, S, ST, WR>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
     if (blk == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_out = t + 1;
 }
 
@@ -685,7 +795,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
 // instance's parameters are staged in shared memory for the tile; its tensor
 // maps are read from the instance table in device memory.  counters[q]
 // serves the steps of parity q; each launch zeroes the other one for the next.
-template <int NW, bool ST>
+template <int NW, bool ST, bool WR>
 __global__ void __launch_bounds__(32 * NW, 1)
     step_batch_kernel(const BatchInstance* __restrict__ insts, const int4* __restrict__ tiles, int ntiles,
                       int parity, const long long* __restrict__ t_in, long long* __restrict__ t_out,
@@ -715,7 +825,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
         // the grid's tensor maps live in device memory, written before the launch
         const TileMaps* maps = &insts[tl.x].maps[parity];
         if (tid == 0) fence_tensormap_acquire(maps);
-        step_tile<NW, float, ST>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
+        step_tile<NW, float, ST, WR>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
                                  partials + 2 * k);
     }
     if (blockIdx.x == 0 && tid == 0) *t_out = t + 1;
@@ -824,7 +934,7 @@ int conv_blocks(const StepParams& p) {
     return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
 }
 
-template <int NW, typename S, bool ST>
+template <int NW, typename S, bool ST, bool WR>
 cudaError_t launch_nw(const StepParams& p, int storage, const void* in, void* out, const long long* t_in,
                       long long* t_out, double* partials, cudaStream_t s, const TileMaps* maps) {
     const LaunchShape sh = step_shape(p, storage);
@@ -833,58 +943,70 @@ cudaError_t launch_nw(const StepParams& p, int storage, const void* in, void* ou
         memset(&none, 0, sizeof(none));
         maps = &none;
     }
-    step2_kernel<NW, S, ST><<<sh.grid, sh.block, sh.smem, s>>>(p, *maps, static_cast<const S*>(in),
-                                                               static_cast<S*>(out), t_in, t_out, partials);
+    step2_kernel<NW, S, ST, WR><<<sh.grid, sh.block, Step2Smem<NW, S, ST, WR>::BYTES, s>>>(
+        p, *maps, static_cast<const S*>(in), static_cast<S*>(out), t_in, t_out, partials);
     return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_step_t(const StepParams& p, int st, const void* in, void* out, const long long* t_in,
                           long long* t_out, double* partials, cudaStream_t s, const TileMaps* m) {
-    if constexpr (sizeof(S) == 4) {  // FP32 blocks of 8 or 12 warps without the staging box
-        if (p.plain_stores && p.block_warps == 8) return launch_nw<8, S, false>(p, st, in, out, t_in, t_out, partials, s, m);
-        if (p.plain_stores && p.block_warps == 12)
-            return launch_nw<12, S, false>(p, st, in, out, t_in, t_out, partials, s, m);
+    if constexpr (sizeof(S) == 4) {  // FP32 blocks of 8 or 12 warps: plain-store and periodic-face forms
+        const bool pl = p.plain_stores != 0, wr = m && m->valid && m->wrap;
+        if (p.block_warps == 8) {
+            if (wr) return pl ? launch_nw<8, S, false, true>(p, st, in, out, t_in, t_out, partials, s, m)
+                              : launch_nw<8, S, true, true>(p, st, in, out, t_in, t_out, partials, s, m);
+            if (pl) return launch_nw<8, S, false, false>(p, st, in, out, t_in, t_out, partials, s, m);
+        }
+        if (p.block_warps == 12) {
+            if (wr) return pl ? launch_nw<12, S, false, true>(p, st, in, out, t_in, t_out, partials, s, m)
+                              : launch_nw<12, S, true, true>(p, st, in, out, t_in, t_out, partials, s, m);
+            if (pl) return launch_nw<12, S, false, false>(p, st, in, out, t_in, t_out, partials, s, m);
+        }
     }
     switch (p.block_warps) {
-        case 8: return launch_nw<8, S, true>(p, st, in, out, t_in, t_out, partials, s, m);
-        case 12: return launch_nw<12, S, true>(p, st, in, out, t_in, t_out, partials, s, m);
-        case 16: return launch_nw<16, S, true>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 8: return launch_nw<8, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 12: return launch_nw<12, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 16: return launch_nw<16, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int NW, typename S, bool ST>
+template <int NW, typename S, bool ST, bool WR>
 cudaError_t prepare_nw() {
-    return cudaFuncSetAttribute(step2_kernel<NW, S, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Step2Smem<NW, S, ST>::BYTES);
+    return cudaFuncSetAttribute(step2_kernel<NW, S, ST, WR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Step2Smem<NW, S, ST, WR>::BYTES);
 }
 
-template <int NW, bool ST>
+template <int NW, bool ST, bool WR>
 cudaError_t launch_batch_nw(const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
                             const long long* t_in, long long* t_out, int* counters, double* partials, int sms,
                             cudaStream_t s) {
-    step_batch_kernel<NW, ST><<<sms, dim3(32, NW, 1), Step2Smem<NW, float, ST>::BYTES, s>>>(
+    step_batch_kernel<NW, ST, WR><<<sms, dim3(32, NW, 1), Step2Smem<NW, float, ST, WR>::BYTES, s>>>(
         insts, tiles, ntiles, parity, t_in, t_out, counters, partials);
     return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t prepare_t() {
-    cudaError_t e = prepare_nw<8, S, true>();
-    if (e == cudaSuccess) e = prepare_nw<12, S, true>();
-    if (e == cudaSuccess) e = prepare_nw<16, S, true>();
+    cudaError_t e = prepare_nw<8, S, true, false>();
+    if (e == cudaSuccess) e = prepare_nw<12, S, true, false>();
+    if (e == cudaSuccess) e = prepare_nw<16, S, true, false>();
     if constexpr (sizeof(S) == 4) {
-        if (e == cudaSuccess) e = prepare_nw<8, S, false>();
-        if (e == cudaSuccess) e = prepare_nw<12, S, false>();
+        if (e == cudaSuccess) e = prepare_nw<8, S, false, false>();
+        if (e == cudaSuccess) e = prepare_nw<12, S, false, false>();
+        if (e == cudaSuccess) e = prepare_nw<8, S, true, true>();
+        if (e == cudaSuccess) e = prepare_nw<12, S, true, true>();
+        if (e == cudaSuccess) e = prepare_nw<8, S, false, true>();
+        if (e == cudaSuccess) e = prepare_nw<12, S, false, true>();
     }
     return e;
 }
 
-template <int NW, bool ST>
+template <int NW, bool ST, bool WR>
 cudaError_t prepare_batch_nw() {
-    return cudaFuncSetAttribute(step_batch_kernel<NW, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Step2Smem<NW, float, ST>::BYTES);
+    return cudaFuncSetAttribute(step_batch_kernel<NW, ST, WR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Step2Smem<NW, float, ST, WR>::BYTES);
 }
 
 }  // namespace
@@ -892,25 +1014,28 @@ cudaError_t prepare_batch_nw() {
 static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied as ints");
 
 cudaError_t prepare_batch_kernels() {
-    cudaError_t e = prepare_batch_nw<8, true>();
-    if (e == cudaSuccess) e = prepare_batch_nw<12, true>();
-    if (e == cudaSuccess) e = prepare_batch_nw<8, false>();
-    if (e == cudaSuccess) e = prepare_batch_nw<12, false>();
+    cudaError_t e = prepare_batch_nw<8, true, false>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12, true, false>();
+    if (e == cudaSuccess) e = prepare_batch_nw<8, false, false>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12, false, false>();
+    if (e == cudaSuccess) e = prepare_batch_nw<8, true, true>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12, true, true>();
+    if (e == cudaSuccess) e = prepare_batch_nw<8, false, true>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12, false, true>();
     return e;
 }
 
-cudaError_t launch_batch_step(int nw, bool plain, const BatchInstance* insts, const int4* tiles, int ntiles,
-                              int parity, const long long* t_in, long long* t_out, int* counters,
+cudaError_t launch_batch_step(int nw, bool plain, bool wrap, const BatchInstance* insts, const int4* tiles,
+                              int ntiles, int parity, const long long* t_in, long long* t_out, int* counters,
                               double* partials, int sms, cudaStream_t s) {
-    const int key = nw * 2 + (plain ? 1 : 0);
-    switch (key) {
-        case 16: return launch_batch_nw<8, true>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
-        case 17: return launch_batch_nw<8, false>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
-        case 24: return launch_batch_nw<12, true>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
-        case 25:
-            return launch_batch_nw<12, false>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s);
-        default: return cudaErrorInvalidValue;
-    }
+#define TSLB_BATCH(NW_, ST_, WR_) \
+    launch_batch_nw<NW_, ST_, WR_>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s)
+    if (nw == 8) return wrap ? (plain ? TSLB_BATCH(8, false, true) : TSLB_BATCH(8, true, true))
+                             : (plain ? TSLB_BATCH(8, false, false) : TSLB_BATCH(8, true, false));
+    if (nw == 12) return wrap ? (plain ? TSLB_BATCH(12, false, true) : TSLB_BATCH(12, true, true))
+                              : (plain ? TSLB_BATCH(12, false, false) : TSLB_BATCH(12, true, false));
+#undef TSLB_BATCH
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t prepare_kernels(int storage) {
@@ -1011,6 +1136,30 @@ cudaError_t make_maps_t(const StepParams& p, const void* buf, const void* obuf, 
     if (r != CUDA_SUCCESS) return cudaSuccess;
     m->valid = 1;
     m->block_warps = nw;
+    if (Step2Smem<8, S>::kFp32 && (p.face[0] == BC_PERIODIC || p.face[2] == BC_PERIODIC)) {
+        // side boxes of ghosts across periodic faces (see step_tile)
+        const cuuint32_t bmx[4] = {4, (cuuint32_t)nr, 1, 10}, bmy[4] = {(cuuint32_t)mw, 1, 1, 10};
+        const cuuint32_t bmc[4] = {4, 1, 1, 10};
+        const cuuint32_t bpx[3] = {4, (cuuint32_t)(nr + 2), 1}, bpy[3] = {(cuuint32_t)pw, 2, 1}, bpc[3] = {4, 2, 1};
+        bool ok = true;
+        auto enc4 = [&](CUtensorMap* t, const cuuint32_t* b) {
+            ok = ok && enc(t, dt, 4, const_cast<void*>(buf), dm, sm, b, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        };
+        auto enc3 = [&](CUtensorMap* t, const cuuint32_t* b) {
+            ok = ok && enc(t, dt, 3, const_cast<void*>(pbase), dm, sm, b, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        };
+        enc4(&m->momx, bmx);
+        enc4(&m->momy, bmy);
+        enc4(&m->momc, bmc);
+        enc3(&m->phix, bpx);
+        enc3(&m->phiy, bpy);
+        enc3(&m->phic, bpc);
+        m->wrap = ok ? 1 : 0;
+    }
     if (Step2Smem<8, S>::kFp32 && obuf && reinterpret_cast<uintptr_t>(obuf) % 16 == 0) {
         const cuuint64_t dout[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz, (cuuint64_t)NFIELDS};
         const cuuint32_t bo[4] = {(cuuint32_t)txs, (cuuint32_t)(nr - 2), 1, (cuuint32_t)NFIELDS};

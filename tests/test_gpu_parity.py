@@ -92,9 +92,9 @@ def test_ragged_tiles_mixed_faces():
 @pytest.mark.parametrize("block_warps", [8, 12, 16])
 def test_periodic_box_rows_droplet(block_warps):
     """A periodic droplet on a grid whose rows are 16-byte aligned (48 x 44 x
-    40): tiles away from the faces move their data by TMA, tiles at the
-    periodic faces (ghost sources across the wrap) element by element, in one
-    launch; every block size."""
+    40): tiles at the periodic faces take the sources of their wrapped ghosts
+    from the side boxes (x strip, y row, corner) loaded with each plane; every
+    block size (16-warp blocks load such tiles element by element)."""
     w = inputs.droplet_workload(48, radius=11.0)
     w.ny, w.nz, w.name = 44, 40, "periodic48x44x40"
     rho0, u0, pi0, _ = inputs.random_smooth_fields(48, 44, 40, seed=31, amp_rho=2e-3, amp_u=2e-2, amp_pi=1e-4)
@@ -126,7 +126,7 @@ def test_periodic_box_rows_mixed_faces():
 @pytest.mark.parametrize("tile_z,block_warps", [(5, 8), (0, 12), (9, 16)])
 def test_periodic_jet_independent_of_tiling(tile_z, block_warps):
     """A jet with periodic sides on an aligned grid: bitwise the same fields for
-    every tiling (TMA and element-wise tiles fall at different places)."""
+    every tiling (side boxes at different tiles, element-wise 16-warp tiles)."""
     w = inputs.jet_workload(56, 48, 40, diameter=10, noise=0.01, seed=5, side="periodic")
     a, _, _ = gpu_run(w, 12)
     b, _, _ = gpu_run(w, 12, tile_z=tile_z, block_warps=block_warps)
