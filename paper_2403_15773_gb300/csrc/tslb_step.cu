@@ -11,9 +11,11 @@
 //   1. reads the moments (rho - 1, u, P) and the phase field of the node and of
 //      its ghost images: one thread loads each plane's boxes with TMA
 //      (cp.async.bulk.tensor, mbarrier completion) a plane or two ahead, and
-//      ghosts of mirror / copy faces read their source inside the box; tiles
-//      whose ghost sources leave the box (periodic wraps) load element by
-//      element (cp.async, or 16-bit loads through registers);
+//      ghosts of mirror / copy faces read their source inside the box; ghosts
+//      across periodic faces read theirs from small side boxes loaded with
+//      the plane (FP32 kernels of 8 and 12 warps); the remaining tiles whose
+//      ghost sources leave the box load element by element (cp.async, or
+//      16-bit loads through registers);
 //   2. evaluates grad phi and its Hessian with the isotropic D3Q27 stencils,
 //      the normal n, the curvature kappa = div n and the surface-tension force
 //      F = -(sigma/2) kappa grad phi (Sec. 2.2);
