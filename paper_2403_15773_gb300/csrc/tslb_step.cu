@@ -55,7 +55,8 @@ namespace {
 // Shared memory of a block of NW warps with storage type S; ST: the staging
 // box of finished planes (FP32 blocks of up to 12 warps; without it, plain
 // stores and a smaller footprint, which leaves the L1 cache more of the
-// storage it shares with shared memory).  The moment and
+// storage it shares with shared memory); WR: each slot also holds the side
+// boxes of ghosts across periodic faces.  The moment and
 // phase-field planes of a tile are held as the boxes a TMA copy writes: a
 // moment box is [10 fields][NR rows][MW columns], a phase-field box
 // [NR + 2 rows][PW columns], each starting at the staged tile's first column
@@ -127,6 +128,8 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 // (bx, by), planes [bz * tile_z, (bz + 1) * tile_z), from state `in` (step t)
 // to state `out`; writes the tile's FP64 partial sums to part[0..1].
 // maps: tensor maps of `in` for TMA loads, or null (element-wise loads).
+// ST: staged TMA stores (FP32); WR: side boxes for ghosts across periodic
+// faces (FP32, maps with the side-box tensor maps).
 template <int NW, typename S, bool ST, bool WR>
 __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
                                           S* __restrict__ out, const long long t, const int bx, const int by,
