@@ -133,10 +133,10 @@ typedef struct {
     int32_t plain_stores;   /* FP32 storage, blocks of 8 or 12 warps: 1 = the step kernel writes each
                                finished plane with plain stores instead of staging it in shared
                                memory for one TMA store; the smaller shared-memory footprint leaves
-                               the L1 cache more room, which tiles at periodic faces use (their
-                               ghost sources lie outside a tensor box, so they load element by
-                               element); 0 = staged TMA stores (default).  Results are the same
-                               either way; tslb_autotune tries both. */
+                               the L1 cache more room for tiles that load element by element
+                               (rows not a multiple of 16 bytes, grids narrower than a tile with
+                               periodic x or y faces); 0 = staged TMA stores (default).  Results
+                               are the same either way; tslb_autotune tries both. */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
                                (blocking, so ordered with the legacy default stream) */
 } tslb_options;
