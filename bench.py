@@ -175,10 +175,11 @@ def cpu_baseline(w, budget_s: float = 12.0):
     sim = oracle.OracleSim(oracle_params_of(s_w))
     rho, u, phi = s_w.fields()
     sim.set_state(rho, u, phi)
+    sim.step(1)                     # the first step also starts the thread pool
     t0 = time.perf_counter()
-    sim.step(1)
-    one = time.perf_counter() - t0
-    n = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    sim.step(3)
+    one = (time.perf_counter() - t0) / 3
+    n = max(1, min(1000, int(budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
     sim.step(n)
     dt = time.perf_counter() - t0
