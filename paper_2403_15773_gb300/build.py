@@ -1,7 +1,7 @@
 """In-tree build of the CUDA library ``_build/libtslb.so`` for sm_103a.
 
-Two translation units are compiled in parallel with nvcc and linked into one
-shared library; the build is skipped when the library is newer than every
+The five translation units are compiled in parallel with nvcc and linked into
+one shared library; the build is skipped when the library is newer than every
 source and header.
 """
 from __future__ import annotations
