@@ -33,7 +33,9 @@ sys.path.insert(0, ROOT)
 METRIC = "GLUPS and % of HBM roofline on 1 GB300, FP32 vs FP16-storage vs batched"
 UNIT = "GLUPS"
 FIELDS = 11  # stored values per node: rho - 1, u (3), P (6), phi
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_jet192_fp32.txt")
+# committed ncu summaries of the step kernel per storage type (DRAM bytes per node)
+PROFILE_SUMMARIES = {"fp32": os.path.join(ROOT, "profiles", "step_kernel_jet192_fp32.txt"),
+                     "fp16": os.path.join(ROOT, "profiles", "step_kernel_jet128_fp16.txt")}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2403_15773_gb300", "csrc", f)
                   for f in ("tslb_step.cu", "tslb_device.cuh", "tslb_internal.h")]
 
@@ -60,12 +62,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(nodes: int):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    scaled to `nodes`, if it was taken on the current kernel source."""
+def profiled_traffic(nodes: int, storage: str = "fp32"):
+    """DRAM bytes per launch of the step kernel of `storage` from its committed
+    ncu summary, scaled to `nodes`, if it was taken on the current kernel
+    source (None for a storage type without one)."""
+    path = PROFILE_SUMMARIES.get(storage)
     try:
-        txt = open(PROFILE_SUMMARY).read()
+        txt = open(path).read() if path else None
     except OSError:
+        return None
+    if txt is None:
         return None
     sha = re.search(r"kernel_source_sha:\s*(\w+)", txt)
     bpn = re.search(r"dram_bytes_per_node:\s*([0-9.eE+-]+)", txt)
@@ -495,7 +501,7 @@ def main():
     per_launch = sec / args.steps
     peak, peak_kind = measured_peaks()
     achieved = bpn * w.nodes / per_launch / 1e9
-    traffic = profiled_traffic(w.nodes)
+    traffic = profiled_traffic(w.nodes, args.storage)
     line = {
         "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,

@@ -66,3 +66,18 @@ def test_reference_arm_line(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["unit"] == "GLUPS" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["metric"] == bench.METRIC
+
+
+def test_profiled_traffic_matches_storage_and_source(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from the ncu summary of the same
+    storage type, taken on the current kernel source, scaled by nodes."""
+    good = tmp_path / "good.txt"
+    good.write_text(f"kernel_source_sha: {bench.kernel_source_sha()}\ndram_bytes_per_node: 80.0\n")
+    stale = tmp_path / "stale.txt"
+    stale.write_text("kernel_source_sha: 0000000000000000\ndram_bytes_per_node: 80.0\n")
+    monkeypatch.setattr(bench, "PROFILE_SUMMARIES", {"fp32": str(good), "fp16": str(stale)})
+    assert bench.profiled_traffic(1000, "fp32") == pytest.approx(80000.0)
+    assert bench.profiled_traffic(1000, "fp16") is None   # taken on other sources
+    assert bench.profiled_traffic(1000, "bf16") is None   # no summary for this storage
+    monkeypatch.setattr(bench, "PROFILE_SUMMARIES", {"fp32": str(tmp_path / "missing.txt")})
+    assert bench.profiled_traffic(1000, "fp32") is None
