@@ -393,3 +393,79 @@ def test_droplet_run_is_well_conditioned():
     assert np.max(np.abs(ma[0] - mb[0])) < 1e-6
     assert np.max(np.abs(ma[1] - mb[1])) / 0.05 < 1e-6
     assert np.max(np.abs(ma[3] - mb[3])) < 1e-6
+
+
+def _inlet_ghost_plane(rho0, u0, pi0, nx, ny, U, D, cx, cy, W):
+    """The ghost node below the inlet face, written out from the non-equilibrium
+    extrapolation of Sec. 2 (Eq. original_neq, neq_final): density and
+    non-equilibrium moment P of the adjacent fluid node x_F (plane z = 0),
+    velocity and phase field imposed (smoothed top hat of diameter D, no
+    noise)."""
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
+    phib = -np.tanh(2.0 * (r - 0.5 * D) / W)
+    s = 0.5 * (1.0 + phib)
+    ub = np.stack([s * U[a] for a in range(3)])
+    return rho0.copy(), ub, pi0.copy(), phib
+
+
+@pytest.mark.parametrize("case", ["imposed_profile", "interface_force"])
+def test_inlet_and_outflow_ghosts_equal_explicit_planes(case):
+    """The inlet ghost carries rho and P of the adjacent fluid node and the
+    imposed u and phi; the outflow ghost is a copy of the last fluid plane.
+    Pinned without the oracle's own ghost code: a box with inlet (-z) and
+    outflow (+z) faces must advance exactly like a z-periodic box two planes
+    taller, whose extra planes hold those ghost states written out
+    explicitly (plane 0: the inlet ghost from rho(z=0), P(z=0), imposed u and
+    phi; plane nz+1: a copy of plane nz-1).  The state is non-uniform
+    everywhere (rho != 1, P != 0, u != 0 next to both faces), so imposing
+    rho = 1 or P = 0 at the inlet, extrapolating from the wrong plane, or
+    copying the outflow from the wrong plane all fail.
+      imposed_profile: a finite nozzle (u and phi vary across the inlet face),
+        sigma = Gamma = 0 so that no interface term reaches a ghost;
+      interface_force: sigma, Gamma != 0 with interfaces inside the box and
+        phi = 1 on the two face planes and on the whole inlet (the periodic
+        twin then sees no interface at its ghost planes either, as the rule
+        says the inlet ghost has none)."""
+    nx, ny, nz = 8, 7, 9
+    omega = 1.7
+    U = (0.01, -0.02, 0.05)
+    W = 3.0
+    rho, u, pi, phi = inputs.random_smooth_fields(nx, ny, nz, seed=23, amp_rho=3e-2, amp_u=3e-2,
+                                                  amp_pi=2e-3)
+    if case == "imposed_profile":
+        sigma, gamma, D, cx, cy = 0.0, 0.0, 5.0, 3.5, 3.0
+    else:
+        sigma, gamma, D, cx, cy = 0.02, 1.0 / W, 1e6, 3.5, 3.0
+        phi[0] = 1.0
+        phi[-1] = 1.0
+    # the state must really differ from the rest state next to both faces
+    assert np.sqrt(np.mean((rho[0] - 1) ** 2)) > 3e-3 and np.sqrt(np.mean(pi[:, 0] ** 2)) > 3e-4
+    assert np.max(np.abs(rho[-1] - rho[-2])) > 1e-3 and np.max(np.abs(pi[:, -1] - pi[:, -2])) > 1e-4
+
+    jet = _sim(nx, ny, nz, omega, sigma, gamma, faces=(P, P, P, P, IN, OUT), inlet_u=U,
+               inlet_diameter=D, inlet_cx=cx, inlet_cy=cy, inlet_width=W, noise_amp=0.0)
+    jet.set_state(rho, u, phi, pi=pi)
+
+    g_rho, g_u, g_pi, g_phi = _inlet_ghost_plane(rho[0], u[:, 0], pi[:, 0], nx, ny, U, D, cx, cy, W)
+    R = np.concatenate([g_rho[None], rho, rho[-1:]], axis=0)
+    UU = np.concatenate([g_u[:, None], u, u[:, -1:]], axis=1)
+    PI = np.concatenate([g_pi[:, None], pi, pi[:, -1:]], axis=1)
+    PH = np.concatenate([g_phi[None], phi, phi[-1:]], axis=0)
+    twin = _sim(nx, ny, nz + 2, omega, sigma, gamma)
+    twin.set_state(R, UU, PH, pi=PI)
+
+    jet.step(1)
+    twin.step(1)
+    a, b = jet.moments(), twin.moments()
+    assert np.max(np.abs(a[0] - b[0][1:-1])) < 1e-14
+    assert np.max(np.abs(a[1] - b[1][:, 1:-1])) < 1e-14
+    assert np.max(np.abs(a[2] - b[2][:, 1:-1])) < 1e-14
+    assert np.max(np.abs(a[3] - b[3][1:-1])) < 1e-14
+    # the ghost planes do enter: without them (a plain z-periodic box of nz
+    # planes) the face planes come out different
+    plain = _sim(nx, ny, nz, omega, sigma, gamma)
+    plain.set_state(rho, u, phi, pi=pi)
+    plain.step(1)
+    c = plain.moments()
+    assert np.max(np.abs(a[0][0] - c[0][0])) > 1e-5 and np.max(np.abs(a[0][-1] - c[0][-1])) > 1e-5
