@@ -1,9 +1,13 @@
 """Throughput benchmark of the fused multicomponent TSLB step on GB300.
 
-Default workload: the axisymmetric jet on a 192 x 192 x 384 grid (nozzle
-D = 16 on the z = 0 face, u = 0.05, Re = 5000, We = 100, 1 % inlet noise,
-free-slip sides, outflow), FP32 storage.  One benchmark step is one lattice
-Boltzmann time step over the whole grid (one fused kernel launch).
+Default workload: the large-jet Weber sweep, four jets on a 512 x 512 x 1024
+grid (268 M nodes each; nozzle D = 40 on the z = 0 face, u = 0.05, Re = 5000,
+We = 10, 100, 500 and 2000 through sigma, 1 % inlet noise, free-slip sides,
+outflow), FP32 storage, all four resident in HBM (94 GB of state).  One
+benchmark step is one lattice Boltzmann time step of each of the four jets
+(four fused kernel launches, 1.07 G lattice updates).  The forms measured
+beside it (16-bit storage, the Chapman-Enskog closure, the paper's two-sweep
+design, the batched ensemble) run on the 192 x 192 x 384 jet.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tslb|reference]
 
@@ -80,6 +84,22 @@ def profiled_traffic(nodes: int, storage: str = "fp32"):
     return float(bpn.group(1)) * nodes
 
 
+def profiled_fp32_ops(storage: str = "fp32"):
+    """FP32 lane operations per lattice update of the step kernel of `storage`
+    from its committed ncu summary (instruction counts), if it was taken on the
+    current kernel source."""
+    path = PROFILE_SUMMARIES.get(storage)
+    try:
+        txt = open(path).read() if path else ""
+    except OSError:
+        return None
+    sha = re.search(r"kernel_source_sha:\s*(\w+)", txt)
+    ops = re.search(r"fp32_lane_ops_per_update:\s*([0-9.eE+-]+)", txt)
+    if not sha or not ops or sha.group(1) != kernel_source_sha():
+        return None
+    return float(ops.group(1))
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples of one GPU during the timed region."""
 
@@ -134,6 +154,14 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- workloads
 
+def workloads_by_name(name: str):
+    """The grids one benchmark step advances (the Weber sweep: four)."""
+    from paper_2403_15773_gb300 import inputs
+    if name == "weber512":
+        return inputs.weber_sweep()
+    return [workload_by_name(name)]
+
+
 def workload_by_name(name: str):
     from paper_2403_15773_gb300 import inputs
     if name == "jet192":
@@ -145,6 +173,17 @@ def workload_by_name(name: str):
     if name == "droplet32":
         return inputs.droplet_workload()
     raise SystemExit(f"unknown workload {name}")
+
+
+def describe_all(ws) -> str:
+    if len(ws) == 1:
+        return describe(ws[0])
+    w = ws[0]
+    wes = "/".join(f"{w.inlet_u[2] ** 2 * w.inlet_diameter / x.sigma:g}" for x in ws)
+    return (f"Weber sweep: {len(ws)} jets {w.nx}x{w.ny}x{w.nz}, We {wes} (sigma "
+            f"{'/'.join(f'{x.sigma:.3g}' for x in ws)}), faces {'/'.join(w.faces)}, omega {w.omega:.6f}, "
+            f"W {w.width:g}, nozzle D {w.inlet_diameter:g}, u {w.inlet_u[2]:g}, noise {w.noise_amp:g}; "
+            f"all resident, one step = one time step of each jet")
 
 
 def describe(w) -> str:
@@ -235,55 +274,88 @@ def stored_bytes_per_node(name: str) -> int:
     return (5 if closure == "chapman_enskog" else FIELDS) * 2 * (4 if st == "fp32" else 2)
 
 
-def run_gpu(args, w, storage: str, rank: int, world: int, dist):
+def run_gpu(args, ws, storage: str, world: int, dist, tile=None, steps=None):
+    """Times `steps` benchmark steps of the grids `ws`, all resident at once:
+    each benchmark step advances every grid by one time step (one fused
+    launch per grid, the grids in turn on one stream).  The tile shape is
+    autotuned on the first grid (unless given) and used for all of them."""
     import torch
     import paper_2403_15773_gb300 as tslb
-    dev = torch.device("cuda", torch.cuda.current_device())
+    steps = args.steps if steps is None else steps
     stream = torch.cuda.Stream()
     st, scheme, closure = variant_form(storage)
     two = scheme == "two_sweep"
-    sim = tslb.Simulation(w, storage=st, stream=stream,
-                          block_warps=0 if two else args.block_warps, tile_z=0 if two else args.tile_z,
-                          scheme=scheme, closure=closure, plain_stores=args.plain_stores and not two)
-    rho, u, phi = w.fields()
-    sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
-    shape = None
-    if not two and not args.block_warps and not args.tile_z:
-        shape = sim.autotune(6)  # tile shape chosen by timing; the state does not change
-    sim.step(args.warmup)
-    sim.synchronize()
+    tile = dict(tile or {})
+    if not tile and not two and (args.block_warps or args.tile_z):
+        tile = {"block_warps": args.block_warps, "tile_z": args.tile_z, "plain_stores": int(args.plain_stores)}
+    cache = {}
+
+    def start_fields(w):  # grids of one jet geometry share their initial fields
+        key = (w.kind, w.nx, w.ny, w.nz, w.radius, w.width)
+        if key not in cache:
+            cache.clear()
+            cache[key] = tuple(torch.from_numpy(a.astype(np.float32)) for a in w.fields())
+        return cache[key]
+
+    def make(w):
+        sim = tslb.Simulation(w, storage=st, stream=stream,
+                              block_warps=0 if two else tile.get("block_warps", 0),
+                              tile_z=0 if two else tile.get("tile_z", 0), scheme=scheme, closure=closure,
+                              plain_stores=bool(tile.get("plain_stores", 0)) and not two)
+        sim.set_state(*start_fields(w))
+        return sim
+
+    sims = [make(ws[0])]
+    tuned = False
+    if not two and not tile:
+        nw, tz, pl = sims[0].autotune(6)  # tile shape chosen by timing; the state does not change
+        tile = {"block_warps": nw, "tile_z": tz, "plain_stores": pl}
+        tuned = True
+    sims += [make(w) for w in ws[1:]]
+    cache.clear()
+    for sim in sims:
+        sim.step(args.warmup)
+        sim.synchronize()
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    launches0 = sim.kernel_launches
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = sum(sim.kernel_launches for sim in sims)
+    start = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in sims]
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")) if world > 1 else torch.cuda.current_device())
     with sampler:
         barrier()
         start.record(stream)
-        sim.step(args.steps)
-        stop.record(stream)
-        stop.synchronize()
+        for sim, mark in zip(sims, marks):
+            sim.step(steps)
+            mark.record(stream)
+        marks[-1].synchronize()
         barrier()
-    ms = start.elapsed_time(stop)
-    launches = sim.kernel_launches - launches0
-    m, p = sim.sums()
-    ok = math.isfinite(m) and math.isfinite(p)
-    ms = max_over_ranks(ms, dist, dev)  # the slowest rank sets the job's time
-    sim.close()
-    return {"ms": ms, "launches": launches, "clocks": sampler.summary(), "finite": ok,
-            "shape": {"block_warps": shape[0], "tile_z": shape[1], "plain_stores": shape[2]} if shape else
-            {"block_warps": args.block_warps or 8, "tile_z": args.tile_z or 0,
-             "plain_stores": int(args.plain_stores)}}
+    ms = start.elapsed_time(marks[-1])
+    per = [start.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, len(marks))]
+    launches = sum(sim.kernel_launches for sim in sims) - launches0
+    ok = True
+    for sim in sims:
+        m, p = sim.sums()
+        ok = ok and math.isfinite(m) and math.isfinite(p)
+        sim.close()
+    del sims
+    torch.cuda.empty_cache()
+    ms = max_over_ranks(ms, dist, torch.device("cuda", torch.cuda.current_device()))
+    if two:
+        tile = {"block_warps": 8, "tile_z": 0, "plain_stores": 0}
+    return {"ms": ms, "per_grid_ms": per, "launches": launches, "clocks": sampler.summary(), "finite": ok,
+            "shape": tile, "autotuned": tuned, "steps": steps}
 
 
 def run_batched(args):
     """The ensemble of independent uneven grids advanced together (one
     persistent launch per step, graph-replayed, autotuned tiles), against the
-    same grids advanced one after another with the plain FP32 path."""
+    same grids advanced one after another with the plain FP32 path, each in
+    the tile shape the autotuner picks for its kind of grid (edge and faces)."""
     import torch
     import paper_2403_15773_gb300 as tslb
     from paper_2403_15773_gb300 import inputs
@@ -306,10 +378,18 @@ def run_batched(args):
     launches = b.kernel_launches - l0
     b.close()
     nodes = sum(w.nodes for w in ws)
+    tuned = {}  # (edge, faces) -> tile shape of the single-grid path
     ms_seq = 0.0
     for w in ws:
-        s = tslb.Simulation(w, stream=stream)
+        key = (w.nx, w.ny, w.nz, tuple(w.faces))
         rho, u, phi = w.fields()
+        if key not in tuned:
+            s = tslb.Simulation(w, stream=stream)
+            s.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
+            tuned[key] = s.autotune(3)
+            s.close()
+        nw, tz, pl = tuned[key]
+        s = tslb.Simulation(w, stream=stream, block_warps=nw, tile_z=tz, plain_stores=bool(pl))
         s.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
         s.step(args.warmup)
         s.synchronize()
@@ -319,6 +399,7 @@ def run_batched(args):
         sp.synchronize()
         ms_seq += st.elapsed_time(sp)
         s.close()
+    torch.cuda.empty_cache()
     g_batch = nodes * steps / (ms_batch * 1e-3) / 1e9
     g_seq = nodes * steps / (ms_seq * 1e-3) / 1e9
     peak, _ = measured_peaks()
@@ -326,63 +407,77 @@ def run_batched(args):
             "unit": UNIT, "ms_per_step": ms_batch / steps,
             "hbm_frac": FIELDS * 8 * nodes / (ms_batch * 1e-3 / steps) / 1e9 / peak,
             "sequential_fp32_value": g_seq, "speedup_vs_sequential_fp32": g_batch / g_seq,
+            "sequential_tiles": "each grid in the tile shape the autotuner picks for its edge and faces "
+                                f"({len(tuned)} kinds), one grid after another on one stream",
             "gpu_launches": launches,
             "autotuned": {"block_warps": shape[0], "tile_z": shape[1], "plain_stores": shape[2]},
             "workload": "64 cubic grids, edges uniform in {48, 64, 96, 128}, periodic droplets (R = edge/4) "
                         "and jets (D = 0.15 edge, periodic sides), We log-uniform in [10, 2000], seed 4"}
 
 
-def run_e2e(args, w, storage: str, world: int = 1, dist=None, shape=None):
-    """Same metric through the public C ABI with host buffers: upload the
-    initial fields from pinned memory, run the steps, read the moments, the
-    phase field and the FP64 sums back into pinned memory.  `shape` is the
-    tile shape of the device-timed run (so both time the same kernel)."""
+def run_e2e(args, ws, storage: str, world: int = 1, dist=None, shape=None):
+    """Same metric through the public C ABI with host buffers: per grid, upload
+    the initial fields from pinned memory, run the steps, read rho, u and phi
+    back into pinned memory and take the FP64 sums.  `shape` is the tile shape
+    of the device-timed run (so both time the same kernel)."""
     import torch
     import paper_2403_15773_gb300 as tslb
     stream = torch.cuda.Stream()
     shape = shape or {}
-    sim = tslb.Simulation(w, storage=storage, stream=stream, block_warps=shape.get("block_warps", 0),
-                          tile_z=shape.get("tile_z", 0), plain_stores=bool(shape.get("plain_stores", 0)))
-    N = w.nodes
-    rho, u, phi = (torch.from_numpy(a.astype(np.float32).reshape(-1)).pin_memory() for a in w.fields())
-    out_rho = torch.empty(N, dtype=torch.float32).pin_memory()
-    out_u = torch.empty(3 * N, dtype=torch.float32).pin_memory()
-    out_pi = torch.empty(6 * N, dtype=torch.float32).pin_memory()
-    out_phi = torch.empty(N, dtype=torch.float32).pin_memory()
-    # warm-up of the whole path (graph capture, first-touch of pinned pages)
-    sim.set_state_host(rho, u, phi)
-    sim.step(min(args.warmup, 16))
-    sim.moments_host(out_rho, out_u, out_pi)
-    sim.phi_host(out_phi)
+    sims = [tslb.Simulation(w, storage=storage, stream=stream, block_warps=shape.get("block_warps", 0),
+                            tile_z=shape.get("tile_z", 0), plain_stores=bool(shape.get("plain_stores", 0)))
+            for w in ws]
+    inputs_of = {}
+    for w in ws:
+        key = (w.kind, w.nx, w.ny, w.nz, w.radius, w.width)
+        if key not in inputs_of:
+            inputs_of[key] = tuple(torch.from_numpy(a.astype(np.float32).reshape(-1)).pin_memory()
+                                   for a in w.fields())
+    nmax = max(w.nodes for w in ws)
+    out_rho = torch.empty(nmax, dtype=torch.float32).pin_memory()
+    out_u = torch.empty(3 * nmax, dtype=torch.float32).pin_memory()
+    out_phi = torch.empty(nmax, dtype=torch.float32).pin_memory()
+
+    def job(steps):
+        for w, sim in zip(ws, sims):
+            rho, u, phi = inputs_of[(w.kind, w.nx, w.ny, w.nz, w.radius, w.width)]
+            sim.set_state_host(rho, u, phi)
+            sim.step(steps)
+            sim.moments_host(out_rho, out_u, None)
+            sim.phi_host(out_phi)
+            sim.sums()
+
+    job(min(args.warmup, 16))  # warm-up of the whole path (graph capture, first touch of pinned pages)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    sim.set_state_host(rho, u, phi)
-    sim.step(args.steps)
-    sim.moments_host(out_rho, out_u, out_pi)
-    sim.phi_host(out_phi)
-    m, p = sim.sums()
+    job(args.steps)
     dt = time.perf_counter() - t0
-    sim.close()
+    for sim in sims:
+        sim.close()
+    del sims
+    torch.cuda.empty_cache()
     dt = max_over_ranks(dt * 1e3, dist, torch.device("cuda", torch.cuda.current_device())) * 1e-3
-    h2d = 5 * N * 4
-    d2h = 11 * N * 4 + 16
-    return {"value": whole_job_rate(N, world, args.steps, dt * 1e3), "unit": UNIT,
+    nodes = sum(w.nodes for w in ws)
+    h2d = 5 * nodes * 4
+    d2h = 5 * nodes * 4 + 16 * len(ws)
+    return {"value": whole_job_rate(nodes, world, args.steps, dt * 1e3), "unit": UNIT,
             "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-            "note": "one job per timed region: set_state from pinned host buffers, the steps, "
-                    "get_moments + get_phi into pinned host buffers, FP64 sums; bytes per step "
+            "note": "one job per timed region: per grid, set_state from pinned host buffers, the steps, "
+                    "get_moments (rho, u) + get_phi into pinned host buffers, FP64 sums; bytes per step "
                     "are the job's copies divided by the steps"}
 
 
-def variant_line(args, w, storage, res, base_glups):
-    glups = w.nodes * args.steps / (res["ms"] * 1e-3) / 1e9
+def variant_line(w, storage, res, base_glups):
+    steps = res["steps"]
+    glups = w.nodes * steps / (res["ms"] * 1e-3) / 1e9
     bpn = stored_bytes_per_node(storage)
     st, scheme, closure = variant_form(storage)
     peak, _ = measured_peaks()
-    ach = bpn * w.nodes / (res["ms"] * 1e-3 / args.steps) / 1e9
+    ach = bpn * w.nodes / (res["ms"] * 1e-3 / steps) / 1e9
     return {"storage": st, "scheme": scheme, "closure": closure, "value": glups, "unit": UNIT,
-            "speedup_vs_fp32": glups / base_glups, "ms_per_step": res["ms"] / args.steps,
+            "speedup_vs_fp32": glups / base_glups, "ms_per_step": res["ms"] / steps, "steps": steps,
             "bytes_per_node": bpn, "hbm_frac": ach / peak, "gpu_launches": res["launches"],
             "tile": res["shape"], "state_gb": (45 * 4 if scheme == "two_sweep" else bpn) * w.nodes / 1e9}
 
@@ -414,27 +509,37 @@ def oracle_errors(w, storages, steps=200):
         sim.close()
         out[name] = {"rho": float(np.max(np.abs(g[0] - r[0])) / np.max(np.abs(r[0]))),
                      "u": float(np.max(np.abs(g[1] - r[1])) / max(np.max(np.abs(r[1])), 0.05)),
-                     "phi": float(np.max(np.abs(g[3] - r[3])))}
-    case = f"{c.nx}x{c.ny}x{c.nz} crop of the workload, {steps} steps, max error (rho / max rho, u / max(max u, 0.05), phi)"
+                     "phi": float(np.max(np.abs(g[3] - r[3]))),
+                     "rho_rms": float(np.sqrt(np.mean((g[0] - r[0]) ** 2)) / np.max(np.abs(r[0]))),
+                     "u_rms": float(np.sqrt(np.mean((g[1] - r[1]) ** 2)) / max(np.max(np.abs(r[1])), 0.05)),
+                     "phi_rms": float(np.sqrt(np.mean((g[3] - r[3]) ** 2)))}
+    case = (f"{c.nx}x{c.ny}x{c.nz} crop of the workload (nozzle D {c.inlet_diameter:g}), {steps} steps; max "
+            f"and rms error (rho / max rho, u / max(max u, 0.05), phi)")
     return out, case
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=500,
+                    help="timed benchmark steps (Weber sweep: one time step of each of the four jets)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="tslb", choices=["tslb", "reference"])
-    ap.add_argument("--workload", default="jet192")
+    ap.add_argument("--workload", default="weber512",
+                    help="weber512 (the four 512x512x1024 jets), jet512 (one of them, We 100), jet192, "
+                         "jet128, droplet32")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
-    ap.add_argument("--variants", default="fp16,bf16,two_sweep,ce,ce_fp16",
-                    help="extra forms measured on the same workload: fp16, bf16 storage, "
+    ap.add_argument("--variants", default="fp32,fp16,bf16,two_sweep,ce,ce_fp16",
+                    help="forms measured on the variant workload: fp32, fp16, bf16 storage, "
                          "two_sweep (the paper's population design), ce, ce_fp16, ce_bf16 (the "
                          "Chapman-Enskog closure, 5 stored fields) ('' for none)")
+    ap.add_argument("--variant-workload", default="jet192")
+    ap.add_argument("--variant-steps", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-fma-peak", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--block-warps", type=int, default=0)
     ap.add_argument("--tile-z", type=int, default=0)
@@ -446,13 +551,13 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    w = workload_by_name(args.workload)
+    ws = workloads_by_name(args.workload)
 
     if args.impl == "reference":
         # the reference arm is the FP64 CPU oracle; under torchrun only rank 0 runs it
         if rank != 0:
             return
-        return reference_arm(args, w)
+        return reference_arm(args, ws)
 
     import torch
     dist = None
@@ -463,31 +568,46 @@ def main():
     import paper_2403_15773_gb300 as tslb
     tslb.lib()  # build / load the CUDA library before timing
 
-    res = run_gpu(args, w, args.storage, rank, world, dist)
-    base_glups = w.nodes * args.steps / (res["ms"] * 1e-3) / 1e9
+    res = run_gpu(args, ws, args.storage, world, dist)
+    nodes = sum(w.nodes for w in ws)
+    e2e = None if args.no_e2e else run_e2e(args, ws, args.storage, world, dist, res["shape"])
+
     variants = {}
-    vlist = [s for s in args.variants.split(",") if s and s != args.storage]
-    for v in vlist:
-        r = run_gpu(args, w, v, rank, world, dist)
-        variants[v] = variant_line(args, w, v, r, base_glups)
+    vlist = [s for s in args.variants.split(",") if s]
+    wv = workload_by_name(args.variant_workload)
+    base_v = None
+    if vlist and world == 1:
+        base = run_gpu(args, [wv], "fp32", world, dist, steps=args.variant_steps)
+        base_v = wv.nodes * base["steps"] / (base["ms"] * 1e-3) / 1e9
+        for v in vlist:
+            r = base if v == "fp32" else run_gpu(args, [wv], v, world, dist, steps=args.variant_steps)
+            variants[v] = variant_line(wv, v, r, base_v)
+            variants[v]["workload"] = describe(wv)
     if not args.no_batched and world == 1:
         variants["batched"] = run_batched(args)
-        variants["batched"]["speedup_vs_fp32"] = variants["batched"]["value"] / base_glups
+        if base_v:
+            variants["batched"]["speedup_vs_fp32"] = variants["batched"]["value"] / base_v
     errs = None
     if rank == 0 and not args.no_oracle_error:
-        errs, err_case = oracle_errors(w, [args.storage] + vlist)
-        for v in vlist:
-            variants[v]["oracle_err"] = errs[v]
+        err_ws = ws[1] if len(ws) > 1 else ws[0]
+        errs, err_case = oracle_errors(err_ws, [args.storage])
+        if vlist:
+            verrs, vcase = oracle_errors(wv, [v for v in vlist])
+            for v in vlist:
+                variants[v]["oracle_err"] = verrs[v]
+                variants[v]["oracle_err_case"] = vcase
     for v in variants:
         if v.startswith("ce"):
             variants[v]["note"] = ("Chapman-Enskog closure of a2_neq (Sec. 2.1): 5 stored fields, P "
                                    "neither stored nor read; a different closure, so oracle_err is "
                                    "against the oracle run with the same closure")
-    if "two_sweep" in variants:
+    if "two_sweep" in variants and base_v:
         variants["two_sweep"]["note"] = ("the paper's design on this GPU: collide+push into 34 population "
                                          "arrays, then their moments; fused speedup over it = "
-                                         f"{base_glups / variants['two_sweep']['value']:.2f}x")
-    e2e = None if args.no_e2e else run_e2e(args, w, args.storage, world, dist, res["shape"])
+                                         f"{base_v / variants['two_sweep']['value']:.2f}x")
+    fma = None
+    if not args.no_fma_peak and rank == 0:
+        fma = {"packed": tslb.tslb_fp32_lane_rate(1), "scalar": tslb.tslb_fp32_lane_rate(0)}
     if dist is not None:
         dist.barrier()
     if rank != 0:
@@ -495,38 +615,55 @@ def main():
             dist.destroy_process_group()
         return
 
+    K = res["steps"]
     sec = res["ms"] * 1e-3
-    glups = whole_job_rate(w.nodes, world, args.steps, res["ms"])
+    glups = whole_job_rate(nodes, world, K, res["ms"])
     bpn = FIELDS * 2 * (4 if args.storage == "fp32" else 2)
-    per_launch = sec / args.steps
+    per_launch = sec / max(res["launches"], 1) if res["launches"] else sec / (K * len(ws))
+    n_grid = ws[0].nodes
     peak, peak_kind = measured_peaks()
-    achieved = bpn * w.nodes / per_launch / 1e9
-    traffic = profiled_traffic(w.nodes, args.storage)
+    achieved = bpn * n_grid / per_launch / 1e9
+    traffic = profiled_traffic(n_grid, args.storage)
     line = {
-        "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.storage == "fp32" else "f32 (" + args.storage + " storage)",
         "data": "synthetic",
-        "config": {"workload": describe(w), "nodes_per_gpu": w.nodes, "storage": args.storage,
-                   "tile": res["shape"],
+        "config": {"workload": describe_all(ws), "grids": len(ws), "nodes_per_grid": n_grid,
+                   "updates_per_step": nodes, "storage": args.storage, "tile": res["shape"],
+                   "tile_autotuned": res["autotuned"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": f"state {bpn * w.nodes / 1e9:.2f} GB (two buffers) > 126 MB L2: "
+                   "l2": f"state {bpn * n_grid / 1e9:.2f} GB per grid (two buffers) > 126 MB L2: "
                          "inputs larger than L2, no flush"},
+        "per_grid": [{"sigma": w.sigma, "value": w.nodes * K / (ms * 1e-3) / 1e9, "ms_per_step": ms / K}
+                     for w, ms in zip(ws, res["per_grid_ms"])],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "note": f"{bpn} algorithmic bytes per node ({FIELDS} stored values read and "
-                             f"written) x {w.nodes} nodes per launch / mean launch time; peak "
-                             f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+                             f"written) x {n_grid} nodes per launch / mean launch time over the timed "
+                             f"region ({res['launches']} launches); peak {peak_kind} (MEASURED_PEAKS.json "
+                             f"hbm_gbs); traffic: ncu DRAM bytes per node of the same kernel scaled to the "
+                             f"grid (null when the kernel changed since the capture)"},
         "oracle_err": None if errs is None else {"case": err_case, args.storage: errs[args.storage]},
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "variants": variants,
     }
+    if fma is not None:
+        ops = profiled_fp32_ops(args.storage)
+        line["fp32_roofline"] = {
+            "bound": "alu", "unit": "FP32 lane-FMA/s", "peak": fma["packed"], "peak_scalar": fma["scalar"],
+            "ops_per_update": ops,
+            "achieved": None if ops is None else ops * n_grid / per_launch,
+            "frac": None if ops is None else ops * n_grid / per_launch / fma["packed"],
+            "note": "peak: this run's tslb_fp32_lane_rate (independent FMA chains; packed f32x2 and "
+                    "scalar); ops_per_update: FP32 lane operations (packed x 2) per lattice update "
+                    "counted by ncu on the same kernel source (null when it changed since)"}
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w)
+        line["cpu_baseline"] = cpu_baseline(ws[1] if len(ws) > 1 else ws[0])
     if not res["finite"]:
         line["error"] = "non-finite sums"
     print(json.dumps(line), flush=True)
@@ -534,25 +671,34 @@ def main():
         dist.destroy_process_group()
 
 
-def reference_arm(args, w):
+def reference_arm(args, ws):
     """The FP64 CPU oracle timed as it stands on the host cores: each benchmark
-    step is one oracle time step of a bounded sample of the workload."""
+    step is one oracle time step of a bounded sample of each grid of the
+    workload (a 32^3 crop around the nozzle)."""
     import oracle
-    s_w = oracle_sample_workload(w, (32, 32, 32))
-    sim = oracle.OracleSim(oracle_params_of(s_w))
-    rho, u, phi = s_w.fields()
-    sim.set_state(rho, u, phi)
-    sim.step(args.warmup)
+    sims = []
+    for w in ws:
+        s_w = oracle_sample_workload(w, (32, 32, 32))
+        sim = oracle.OracleSim(oracle_params_of(s_w))
+        rho, u, phi = s_w.fields()
+        sim.set_state(rho, u, phi)
+        sims.append((s_w, sim))
+    for _, sim in sims:
+        sim.step(args.warmup)
     t0 = time.perf_counter()
-    sim.step(args.steps)
+    for _, sim in sims:
+        sim.step(args.steps)
     dt = time.perf_counter() - t0
-    v = s_w.nodes * args.steps / dt / 1e9
-    cb = {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-          "sample": f"{s_w.nx}x{s_w.ny}x{s_w.nz} crop of the workload around the nozzle per step"}
+    nodes = sum(s_w.nodes for s_w, _ in sims)
+    v = nodes * args.steps / dt / 1e9
+    s0 = sims[0][0]
+    sample = (f"{s0.nx}x{s0.ny}x{s0.nz} crop around the nozzle of each of the {len(ws)} grid(s) of the "
+              f"workload per step")
+    cb = {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle", "sample": sample}
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": {"workload": describe(w), "sample": cb["sample"]},
+            "impl": "reference", "config": {"workload": describe_all(ws), "sample": sample},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -128,8 +128,11 @@ typedef struct {
     int32_t closure;        /* tslb_closure of the non-equilibrium second moment; default
                                TSLB_CLOSURE_PROJECTION */
     int32_t test_tma_stall; /* testing only: 1 makes the step kernel's TMA tiles wait for bytes no copy
-                               delivers, so its bounded wait expires (about 1 s per block) and
-                               tslb_sums returns TSLB_ERR_TIMEOUT; 0 = off (default) */
+                               delivers in their first loads, so the bounded wait expires (about
+                               1 s per block) and tslb_sums returns TSLB_ERR_TIMEOUT; 2 does the
+                               same to the first loads of the plane march, so the tile gives up
+                               with later loads still in flight (it lets them land before it
+                               releases its barriers); 0 = off (default) */
     int32_t plain_stores;   /* FP32 storage, blocks of 8 or 12 warps: 1 = the step kernel writes each
                                finished plane with plain stores instead of staging it in shared
                                memory for one TMA store; the smaller shared-memory footprint leaves
@@ -273,12 +276,29 @@ TSLB_API tslb_status tslb_autotune(tslb_ctx* ctx, int32_t steps_per_trial, int32
  * the library until the process exits.  n must lie in [1, 268435456] (16384
  * partials of 16384 values; 512 x 512 x 1024 nodes); larger n returns
  * TSLB_ERR_INVALID_ARG without launching anything.  The first call on a device
- * looks up the scratch's device address, so make it before any stream capture.
- * All calls share the scratch: calls whose work overlaps on the GPU race on it
- * and must be ordered by the caller (same stream, or events).  Returns
- * TSLB_ERR_CUDA if a launch fails; messages via tslb_last_error(NULL). */
+ * is its set-up: it looks up the scratch's device address, which the library
+ * keeps until the process exits, and with CUDA's lazy module loading it is
+ * also the call that loads the library's kernels onto the device (which may
+ * allocate and synchronise once).  So make a first call on each device before
+ * any stream capture and before any section that must not allocate, and do not
+ * reset the device (cudaDeviceReset) while the process still uses this entry
+ * point.  All calls share the scratch: calls whose work overlaps on the GPU
+ * race on it and must be ordered by the caller (same stream, or events).
+ * Returns TSLB_ERR_CUDA if a launch fails; messages via tslb_last_error(NULL). */
 TSLB_API tslb_status tslb_field_sums_noalloc(const float* rho, const float* phi, int64_t n,
                                              double* out, void* cuda_stream);
+
+/* Measurement helper (the paper has no counterpart): the FP32 fused
+ * multiply-add rate of the current device, the arithmetic roofline of the
+ * step kernel (whose collision and streaming sweeps are FP32 work).  Runs a
+ * kernel of independent FMA chains in registers on 4 blocks of 512 threads
+ * per SM, scalar FFMA (packed = 0) or packed fma.rn.f32x2 (packed = 1), on
+ * cuda_stream (NULL = legacy default stream), times its second launch with
+ * CUDA events and synchronises.  *lane_ops_per_s = fused multiply-adds per
+ * second summed over all lanes (a packed instruction counts two).  Returns
+ * TSLB_ERR_INVALID_ARG for packed outside {0, 1} or a NULL result pointer,
+ * TSLB_ERR_CUDA if a CUDA call fails; messages via tslb_last_error(NULL). */
+TSLB_API tslb_status tslb_fp32_lane_rate(int32_t packed, void* cuda_stream, double* lane_ops_per_s);
 
 #ifdef __cplusplus
 }

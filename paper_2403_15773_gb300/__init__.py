@@ -29,7 +29,8 @@ __all__ = [
     "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
     "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
     "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
-    "tslb_get_averages", "tslb_reset_averages", "Simulation", "BatchSimulation", "SYMBOLS",
+    "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate", "Simulation", "BatchSimulation",
+    "SYMBOLS",
 ]
 
 TSLB_OK, TSLB_ERR_INVALID_ARG, TSLB_ERR_OOM, TSLB_ERR_CUDA, TSLB_ERR_UNSTABLE, TSLB_ERR_TIMEOUT, \
@@ -45,7 +46,7 @@ SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_se
            "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
            "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
            "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
-           "tslb_get_averages", "tslb_reset_averages")
+           "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate")
 
 
 class Grid(ctypes.Structure):
@@ -131,6 +132,8 @@ def lib() -> ctypes.CDLL:
             L.tslb_get_averages.restype = ctypes.c_int
             L.tslb_reset_averages.argtypes = [VP]
             L.tslb_reset_averages.restype = ctypes.c_int
+            L.tslb_fp32_lane_rate.argtypes = [ctypes.c_int32, VP, P(ctypes.c_double)]
+            L.tslb_fp32_lane_rate.restype = ctypes.c_int
             for name in ("tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments", "tslb_batch_get_phi",
                          "tslb_batch_sums", "tslb_autotune"):
                 getattr(L, name).restype = ctypes.c_int
@@ -299,6 +302,14 @@ def tslb_reset_averages(ctx: int):
     _check(lib().tslb_reset_averages(ctx), ctx)
 
 
+def tslb_fp32_lane_rate(packed: int, stream: int = 0) -> float:
+    """FP32 fused multiply-adds per second of the current device over all
+    lanes (packed = 1: the packed f32x2 form); synchronises."""
+    r = ctypes.c_double()
+    _check(lib().tslb_fp32_lane_rate(int(packed), stream or None, ctypes.byref(r)), None)
+    return r.value
+
+
 # ------------------------------------------------------------ convenience
 
 def _boundary_from(workload) -> Boundary:
@@ -326,7 +337,7 @@ class Simulation:
     def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
                  graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0,
                  average: bool = False, scheme: str = "fused", closure: str = "projection",
-                 test_tma_stall: bool = False, plain_stores: bool = False):
+                 test_tma_stall: int = 0, plain_stores: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Simulation needs a CUDA device")
@@ -345,7 +356,7 @@ class Simulation:
         o.average = 1 if average else 0
         o.scheme = {"fused": 0, "two_sweep": 1}[scheme]
         o.closure = CLOSURES[closure]
-        o.test_tma_stall = 1 if test_tma_stall else 0
+        o.test_tma_stall = int(test_tma_stall)
         o.plain_stores = 1 if plain_stores else 0
         self.closure = closure
         if field_scale is not None:

@@ -1,6 +1,6 @@
 """In-tree build of the CUDA library ``_build/libtslb.so`` for sm_103a.
 
-The five translation units are compiled in parallel with nvcc and linked into
+The six translation units are compiled in parallel with nvcc and linked into
 one shared library; the build is skipped when the library is newer than every
 source and header.
 """
@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libtslb.so")
-SOURCES = ["tslb_step.cu", "tslb_step_ce.cu", "tslb_api.cu", "tslb_noalloc.cu", "tslb_twosweep.cu"]
+SOURCES = ["tslb_step.cu", "tslb_step_ce.cu", "tslb_api.cu", "tslb_noalloc.cu", "tslb_twosweep.cu",
+           "tslb_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE, "-I" + CSRC]

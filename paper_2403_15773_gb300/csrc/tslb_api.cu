@@ -197,6 +197,10 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
         why = "the Chapman-Enskog closure runs blocks of 8 or 12 warps";
         return false;
     }
+    if (opt->test_tma_stall < 0 || opt->test_tma_stall > 2) {
+        why = "test_tma_stall must be 0, 1 or 2";
+        return false;
+    }
     if (opt->plain_stores != 0 && opt->plain_stores != 1) {
         why = "plain_stores must be 0 or 1";
         return false;
@@ -212,7 +216,7 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     for (int k = 0; k < 6; ++k) p.face[k] = b.face[k];
     p.block_warps = opt->block_warps > 0 ? opt->block_warps : 12;
     p.closure = opt->closure;
-    p.test_stall = opt->test_tma_stall ? 1 : 0;
+    p.test_stall = opt->test_tma_stall;
     p.plain_stores = opt->plain_stores;
     p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz)
                                : auto_tile_z(grid, p.block_warps, default_tile_width(opt), device_sms());

@@ -43,7 +43,8 @@ struct StepParams {
     float inv_scale[NFIELDS];
     double* avg;             // time sums of phi and u_z (2 blocks of fstride doubles) or null
     int* err;                // set to 1 by a kernel whose bounded wait for its tile data gave up
-    int test_stall;          // testing: TMA tiles expect bytes no copy delivers (the wait expires)
+    int test_stall;          // testing: TMA tiles expect bytes no copy delivers, in their first
+                             // loads (1) or in the first loads of the march (2): the wait expires
     int plain_stores;        // FP32, 8 or 12 warps: plain stores instead of the staging box + TMA store
 };
 

@@ -90,8 +90,12 @@ __global__ void __launch_bounds__(kThreads) chunk_finish_kernel(const double* __
 }
 
 // Device address of the scratch array on the current device, looked up once
-// per device.  In host code the name g_partials is only a host-side stand-in,
-// not an address the GPU can use.
+// per device (the set-up of the first call on that device) and kept until the
+// process exits.  In host code the name g_partials is only a host-side
+// stand-in, not an address the GPU can use.  The cached address belongs to the
+// device's primary context: a caller that resets the device (cudaDeviceReset)
+// and goes on using this library in the same process would hand the kernels
+// an address that is no longer mapped, so the device must not be reset.
 cudaError_t scratch_on(int device, double** ptr) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mutex);

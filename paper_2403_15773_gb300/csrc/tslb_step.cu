@@ -126,12 +126,14 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 
 // One tile of one time step: the 28 x (2 NW - 2) interior columns at tile
 // (bx, by), planes [bz * tile_z, (bz + 1) * tile_z), from state `in` (step t)
-// to state `out`; writes the tile's FP64 partial sums to part[0..1].
+// to state `out`; writes the tile's FP64 partial sums to part[0..1].  Returns
+// false (in every thread) if tile loads were still in flight when the block
+// gave up on them: its mbarriers and shared memory must then not be reused.
 // maps: tensor maps of `in` for TMA loads, or null (element-wise loads).
 // ST: staged TMA stores (FP32); WR: side boxes for ghosts across periodic
 // faces (FP32, maps with the side-box tensor maps).
 template <int NW, typename S, bool ST, bool WR>
-__device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
+__device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
                                           S* __restrict__ out, const long long t, const int bx, const int by,
                                           const int bz, double* __restrict__ part) {
     using L = Step2Smem<NW, S, ST, WR>;
@@ -336,7 +338,10 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
                 float sg;
                 int in2 = 0;
                 fence_proxy_async();
-                mbar_expect_tx(bar + kb, (lp ? pbytes : 0u) + (do_m ? mbytes : 0u));
+                // (P.test_stall == 2: the first loads of the march expect 16 bytes more
+                // than they deliver, so the march gives up with later loads in flight)
+                mbar_expect_tx(bar + kb, (lp ? pbytes : 0u) + (do_m ? mbytes : 0u) +
+                                             (P.test_stall == 2 && qm == z0 - 1 + PF ? 16u : 0u));
                 if (lp) {
                     const int z = resolve_axis(qp, nz, P.face[4], P.face[5], sg, in2);
                     tma_load_3d(ring + pslot(qp) * PSL, &maps->phi, xp, yp, z, bar + kb);
@@ -447,8 +452,8 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
             for (int q = z0 - 2; q <= z0 + PF; ++q)
                 if (!(inlet_face && q < 0)) bytes += pbytes;
             fence_proxy_async();
-            // (P.test_stall: 16 bytes more than the copies deliver, so the wait below expires)
-            mbar_expect_tx(bar + BPRO, bytes + (P.test_stall ? 16u : 0u));
+            // (P.test_stall == 1: 16 bytes more than the copies deliver, so the wait below expires)
+            mbar_expect_tx(bar + BPRO, bytes + (P.test_stall == 1 ? 16u : 0u));
             for (int q = z0 - 2; q <= z0 + PF; ++q)
                 if (!(inlet_face && q < 0)) {
                     const int z = resolve_axis(q, nz, P.face[4], P.face[5], sg, in2);
@@ -743,8 +748,6 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
     }
     // the last plane (z1 - 1) waits in its staging box
     __syncthreads();
-    if (use_maps && tid == 0)  // the next tile of a persistent block initialises them again
-        for (int k = 0; k < NB; ++k) mbar_inval(bar + k);
     if (tst && tid == 0) {
         if (!dead) {
             tma_store_4d(&maps->out, outb + ((z1 - 1 + 8) & 1) * OSL, x0, y0, z1 - 1, 0);
@@ -753,9 +756,17 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         bulk_wait<0>();
     }
     cp_async_wait<0>();
-    // copies still in flight after a failed wait: give them a bounded chance to land
+    // Loads still in flight after a failed wait (the march stopped early):
+    // give them a bounded chance to land before the mbarriers are invalidated,
+    // since a copy must not complete on an invalidated barrier.  If one does
+    // not land, the barriers are left as they are and the tile reports it.
+    bool drained = true;
     for (int k = 0; k < NB; ++k)
-        if ((pend >> k) & 1u) mbar_wait(bar + k, (phase >> k) & 1u);
+        if ((pend >> k) & 1u) drained = mbar_wait(bar + k, (phase >> k) & 1u) && drained;
+    const bool clean = __syncthreads_and(drained) != 0;
+    if (use_maps && tid == 0 && clean)  // the next tile of a persistent block initialises them again
+        for (int k = 0; k < NB; ++k) mbar_inval(bar + k);
+    if (!clean && tid == 0 && P.err) *P.err = 1;
 
     double a = sum_rho, b = sum_phi;
 #pragma unroll
@@ -780,6 +791,7 @@ __device__ __forceinline__ void step_tile(const StepParams& P, const TileMaps* m
         part[1] = B;
     }
     __syncthreads();  // shared memory is reused by the block's next tile
+    return clean;
 }
 
 // One time step of one grid: one block per tile.
@@ -830,8 +842,9 @@ __global__ void __launch_bounds__(32 * NW, 1)
         // the grid's tensor maps live in device memory, written before the launch
         const TileMaps* maps = &insts[tl.x].maps[parity];
         if (tid == 0) fence_tensormap_acquire(maps);
-        step_tile<NW, float, ST, WR>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
-                                 partials + 2 * k);
+        if (!step_tile<NW, float, ST, WR>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
+                                          partials + 2 * k))
+            break;  // loads that never landed: take no further tile into this shared memory
     }
     if (blockIdx.x == 0 && tid == 0) *t_out = t + 1;
 }

@@ -2,7 +2,8 @@
 of j, 5 stored fields) on the GPU with the FP64 oracle run with the same
 closure.  Same error norms and bar as the projection closure: rho relative to
 max|rho|, u relative to max(max|u|, 0.05), phi absolute, 1e-5 after 100
-steps."""
+steps; and on their own scales u relative to max|u_ref| (where that exceeds
+1e-4) and the stored rho - 1 relative to max|rho_ref - 1|."""
 import numpy as np
 import pytest
 import torch
@@ -24,6 +25,9 @@ def gpu_run(w, steps, fields=None, **kw):
                   torch.from_numpy(np.asarray(phi)))
     sim.step(steps)
     out = sim.fields_numpy()
+    if kw.get("storage", "fp32") == "fp32":  # the stored rho - 1 (raw state, field 0)
+        raw = sim.get_state()[:4 * w.nodes].view(torch.float32)
+        out = out + (raw.double().cpu().numpy().reshape(out[0].shape),)
     sums = sim.sums()
     launches = sim.kernel_launches
     sim.close()
@@ -44,10 +48,16 @@ def check_parity(w, steps, fields=None, **kw):
     s.step(steps)
     r = s.moments()
     e = errors(g, r)
+    umax = np.max(np.abs(r[1]))
+    eu = np.max(np.abs(g[1] - r[1])) / umax if umax > 1e-4 else None
+    d_gpu = g[4] if len(g) > 4 else g[0] - 1.0
+    ed = np.max(np.abs(d_gpu - (r[0] - 1.0))) / np.max(np.abs(r[0] - 1.0))
     print(f"CE parity {w.name} {w.nx}x{w.ny}x{w.nz} {steps} steps: err rho {e[0]:.2e} u {e[1]:.2e} "
-          f"phi {e[2]:.2e}")
+          f"phi {e[2]:.2e} | own scale: u {'-' if eu is None else f'{eu:.2e}'}, rho-1 {ed:.2e}")
     assert launches == steps
     assert max(e) < TOL, f"{w.name}: err rho {e[0]:.2e} u {e[1]:.2e} phi {e[2]:.2e}"
+    assert eu is None or eu < TOL, f"{w.name}: err u on max|u_ref| {eu:.2e}"
+    assert ed < TOL, f"{w.name}: err rho - 1 on max|rho_ref - 1| {ed:.2e}"
     m_ref, p_ref, _ = s.sums()
     assert abs(sums[0] - m_ref) / m_ref < 1e-6
     assert abs(sums[1] - p_ref) / np.sum(np.abs(r[3])) < 1e-6

@@ -2,7 +2,10 @@
 
 Error norm (max over the grid): rho relative to max|rho|, u relative to
 max(max|u|, 0.05) (the jet speed), phi absolute (phi in [-1, 1]).  The FP32
-step must match the oracle to 1e-5 after 100 steps."""
+step must match the oracle to 1e-5 after 100 steps.  Besides, on the scale of
+the quantities themselves: u relative to max|u_ref| wherever that exceeds
+1e-4, and the density deviation rho - 1 (which carries the pressure)
+relative to max|rho_ref - 1|, both to the same 1e-5."""
 import numpy as np
 import pytest
 import torch
@@ -23,6 +26,9 @@ def gpu_run(w, steps, fields=None, storage="fp32", pi=None, **kw):
                   torch.from_numpy(np.asarray(phi)), None if pi is None else torch.from_numpy(pi))
     sim.step(steps)
     out = sim.fields_numpy()
+    if storage == "fp32":  # the stored rho - 1 itself (get_moments returns rho, rounded to FP32 near 1)
+        raw = sim.get_state()[:4 * w.nodes].view(torch.float32)
+        out = out + (raw.double().cpu().numpy().reshape(out[0].shape),)
     sums = sim.sums()
     launches = sim.kernel_launches
     sim.close()
@@ -36,6 +42,36 @@ def errors(g, r):
     return e_rho, e_u, e_phi
 
 
+U_FLOOR = 1e-4  # below this max |u_ref| the velocity has no scale of its own
+
+
+def own_scale_errors(g, r):
+    """(u on max|u_ref| or None if max|u_ref| <= 1e-4, rho - 1 on max|rho_ref - 1|).
+    The density deviation is taken from the stored rho - 1 (g[4], the raw FP32
+    state) where the run returned it: rho itself, as get_moments returns it, is
+    rounded to FP32 near 1, i.e. to 2^-24 ~ 6e-8 absolute, which is already
+    1e-5 of a deviation of 6e-3."""
+    umax = np.max(np.abs(r[1]))
+    e_u = np.max(np.abs(g[1] - r[1])) / umax if umax > U_FLOOR else None
+    d_ref = r[0] - 1.0
+    d_gpu = g[4] if len(g) > 4 else g[0] - 1.0
+    e_d = np.max(np.abs(d_gpu - d_ref)) / np.max(np.abs(d_ref))
+    return e_u, e_d
+
+
+def assert_parity(g, r, name, own_scale=True):
+    e = errors(g, r)
+    eu, ed = own_scale_errors(g, r)
+    print(f"parity {name}: err rho {e[0]:.2e} u {e[1]:.2e} phi {e[2]:.2e} | own scale: u "
+          f"{'-' if eu is None else f'{eu:.2e}'} (max|u| {np.max(np.abs(r[1])):.2e}), rho-1 {ed:.2e} "
+          f"(max|rho-1| {np.max(np.abs(r[0] - 1)):.2e})")
+    assert max(e) < TOL, f"{name}: err rho {e[0]:.2e} u {e[1]:.2e} phi {e[2]:.2e}"
+    if own_scale:
+        assert eu is None or eu < TOL, f"{name}: err u on max|u_ref| {eu:.2e}"
+        assert ed < TOL, f"{name}: err rho - 1 on max|rho_ref - 1| {ed:.2e}"
+    return e
+
+
 def check_parity(w, steps, fields=None, pi=None):
     g, sums, launches = gpu_run(w, steps, fields, pi=pi)
     s = oracle_sim(w, fields=fields) if pi is None else None
@@ -45,11 +81,8 @@ def check_parity(w, steps, fields=None, pi=None):
         s.set_state(rho, u, phi, pi=pi)
     s.step(steps)
     r = s.moments()
-    e = errors(g, r)
-    print(f"parity {w.name} {w.nx}x{w.ny}x{w.nz} {steps} steps: err rho {e[0]:.2e} u {e[1]:.2e} "
-          f"phi {e[2]:.2e}")
+    e = assert_parity(g, r, f"{w.name} {w.nx}x{w.ny}x{w.nz} {steps} steps")
     assert launches == steps
-    assert max(e) < TOL, f"{w.name}: err rho {e[0]:.2e} u {e[1]:.2e} phi {e[2]:.2e}"
     # P is a small quantity; compare it on the scale of its own magnitude
     e_pi = np.max(np.abs(g[2] - r[2])) / max(np.max(np.abs(r[2])), 1e-8)
     assert e_pi < 1e-3, f"{w.name}: err P {e_pi:.2e}"
@@ -75,6 +108,28 @@ def test_jet_crop_of_the_192x192x384_geometry():
     """A 64^3 crop of the jet workload (D = 16, omega 1.998, sigma 4e-4, noise 1 %)."""
     w = inputs.crop_jet(inputs.jet_workload(), 64, 64, 64)
     check_parity(w, 100)
+
+
+@pytest.mark.parametrize("dims", [(48, 40, 44), (33, 17, 29)])
+def test_inlet_next_to_a_nonuniform_state(dims):
+    """The inlet's non-equilibrium extrapolation (Eq. original_neq) on a state
+    that is far from the rest state next to the inlet: rho != 1, P != 0 and
+    u != 0 at z = 0, so the ghost's rho and P taken from the adjacent fluid
+    node differ from any imposed value; outflow at +z next to planes that
+    differ; a droplet of component A in bulk B.  One step, then 100, against
+    the oracle (aligned rows: TMA tiles; 33 columns: element-wise tiles).
+    (A random phase field everywhere instead of the droplet makes the case
+    ill-conditioned: the oracle itself, perturbed by 1e-7 in FP64, moves phi
+    by 3.5e-4 within 100 steps on the 48 x 40 x 44 box.)"""
+    nx, ny, nz = dims
+    w = inputs.jet_workload(nx, ny, nz, diameter=10, we=100, noise=0.01, seed=12)
+    w.name = f"inlet_nonuniform{nx}x{ny}x{nz}"
+    rho0, u0, pi0, _ = inputs.random_smooth_fields(nx, ny, nz, seed=41, amp_rho=2e-2, amp_u=2e-2,
+                                                    amp_pi=1e-3)
+    _, _, phi = inputs.droplet_fields(nx, ny, nz, min(nx, ny) / 4.0, 3.0, center=(nx / 2.0, ny / 2.0, 0.6 * nz))
+    assert np.sqrt(np.mean((rho0[0] - 1) ** 2)) > 3e-3 and np.sqrt(np.mean(pi0[:, 0] ** 2)) > 1e-4
+    for steps in (1, 100):
+        check_parity(w, steps, fields=(rho0, u0, phi), pi=pi0)
 
 
 def test_ragged_tiles_mixed_faces():
@@ -103,8 +158,7 @@ def test_periodic_box_rows_droplet(block_warps):
     s = oracle.OracleSim(oracle_params(w))
     s.set_state(rho0, u0, phi, pi=pi0)
     s.step(60)
-    e = errors(g, s.moments())
-    assert max(e) < TOL, f"err rho {e[0]:.2e} u {e[1]:.2e} phi {e[2]:.2e}"
+    assert_parity(g, s.moments(), f"periodic48x44x40 {block_warps} warps 60 steps")
 
 
 def test_periodic_box_rows_mixed_faces():
@@ -391,16 +445,19 @@ def test_non_finite_state_is_reported():
     s2.close()
 
 
-def test_bounded_tma_wait_reports_timeout():
+@pytest.mark.parametrize("stall", [1, 2])
+def test_bounded_tma_wait_reports_timeout(stall):
     """Failure detection of the tile loads without any GPU fault: with the
     testing option the TMA mbarrier of a tile expects 16 bytes more than its
     copies deliver, so the kernel's bounded wait expires (about 1 s), the block
     finishes without further waits, and tslb_sums reports TSLB_ERR_TIMEOUT.
-    All copies have landed when the block exits; a new context then steps
-    normally on the same device."""
+    stall 1: the prologue's loads; stall 2: the first loads of the march, so
+    the block gives up while later planes' loads are in flight and must let
+    them land before it releases its mbarriers.  All copies have landed when
+    the block exits; a new context then steps normally on the same device."""
     w = inputs.jet_workload(28, 14, 8, diameter=6, noise=0.0, seed=2, steps=1)
     rho, u, phi = w.fields()
-    sim = tslb.Simulation(w, block_warps=8, graph_steps=1, test_tma_stall=True)
+    sim = tslb.Simulation(w, block_warps=8, graph_steps=1, test_tma_stall=stall)
     sim.set_state(torch.from_numpy(rho), torch.from_numpy(u), torch.from_numpy(phi))
     sim.step(1)
     with pytest.raises(tslb.TslbError) as ei:
@@ -431,8 +488,8 @@ def test_two_sweep_scheme_parity(case):
     s = oracle_sim(w)
     s.step(100)
     r = s.moments()
-    e = errors(g, r)
-    print(f"parity two-sweep {w.name} 100 steps: err rho {e[0]:.2e} u {e[1]:.2e} phi {e[2]:.2e}")
-    assert max(e) < TOL
+    # (the ablation sums 27 FP32 populations per moment and returns rho, not
+    # rho - 1: it is held to the common norm only, not to the own-scale one)
+    assert_parity(g, r, f"two-sweep {w.name} 100 steps", own_scale=False)
     m_ref, p_ref, _ = s.sums()
     assert abs(sums[0] - m_ref) / m_ref < 1e-6
