@@ -115,9 +115,11 @@ typedef struct {
                                a block marches; batches: 64) */
     int32_t graph_steps;    /* steps per captured CUDA graph replayed by tslb_step; 0 = automatic,
                                1 = plain launches */
-    int32_t block_warps;    /* warps per block of the step kernel: 8, 12 or 16 (tiles of 14, 22 or
-                               30 interior rows; 28 interior columns); 0 = 12 for a single
-                               grid, 8 for a batch */
+    int32_t block_warps;    /* warps per block of the step kernel: 8, 12, 14 or 16 (tiles of 14,
+                               22, 26 or 30 interior rows; 28 interior columns; 14 and 16 keep
+                               part of each thread's state in tensor memory); 0 = 12 for a
+                               single grid, 8 for a batch.  14 and 16: single grids under the
+                               projection closure */
     int32_t scheme;         /* 0: the fused moment-only step (default, 88 B per update in FP32);
                                1: the paper's two-sweep design kept as an ablation: collide+push
                                into 34 population arrays in HBM, then their moments (360 B per
@@ -133,7 +135,7 @@ typedef struct {
                                same to the first loads of the plane march, so the tile gives up
                                with later loads still in flight (it lets them land before it
                                releases its barriers); 0 = off (default) */
-    int32_t plain_stores;   /* FP32 storage, blocks of 8 or 12 warps: 1 = the step kernel writes each
+    int32_t plain_stores;   /* FP32 storage, blocks of 8, 12 or 16 warps: 1 = the step kernel writes each
                                finished plane with plain stores instead of staging it in shared
                                memory for one TMA store; the smaller shared-memory footprint leaves
                                the L1 cache more room for tiles that load element by element
@@ -249,8 +251,8 @@ TSLB_API tslb_status tslb_get_averages(tslb_ctx* ctx, int32_t instance, double* 
 TSLB_API tslb_status tslb_reset_averages(tslb_ctx* ctx);
 
 /* Tile-shape autotuner: times the step kernel for blocks of 8 and 12 warps
- * (and 16 for one grid under the projection closure; with FP32 storage under
- * the projection closure also the 8- and 12-warp forms with plain_stores) and
+ * (and 14 and 16 for one grid under the projection closure; with FP32 storage under
+ * the projection closure also the 8-, 12- and 16-warp forms with plain_stores) and
  * z slabs of 16, 24, 32, 48 and 64 planes, plus, for one grid, the slab
  * depths whose block count fills 2 to 8 waves of one block per SM to at least
  * 90 % (steps_per_trial launches each, CUDA events on the context stream), and

@@ -185,15 +185,16 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
         why = "tile_z must be >= 0";
         return false;
     }
-    if (opt->block_warps != 0 && opt->block_warps != 8 && opt->block_warps != 12 && opt->block_warps != 16) {
-        why = "block_warps must be 0, 8, 12 or 16";
+    if (opt->block_warps != 0 && opt->block_warps != 8 && opt->block_warps != 12 && opt->block_warps != 14 &&
+        opt->block_warps != 16) {
+        why = "block_warps must be 0, 8, 12, 14 or 16";
         return false;
     }
     if (opt->closure != TSLB_CLOSURE_PROJECTION && opt->closure != TSLB_CLOSURE_CHAPMAN_ENSKOG) {
         why = "unknown closure";
         return false;
     }
-    if (opt->closure == TSLB_CLOSURE_CHAPMAN_ENSKOG && opt->block_warps == 16) {
+    if (opt->closure == TSLB_CLOSURE_CHAPMAN_ENSKOG && opt->block_warps > 12) {
         why = "the Chapman-Enskog closure runs blocks of 8 or 12 warps";
         return false;
     }
@@ -926,19 +927,23 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     if (c->scheme == 1) return bad(c, "the two-sweep scheme has no tile shape to tune");
     CK(cudaSetDevice(c->device), "set device");
     const int q = c->cur;
-    // kernel forms tried: blocks of 8 and 12 warps (16 for one grid under the
-    // projection closure), and for FP32 storage under the projection closure
-    // the 8- and 12-warp forms with plain stores as well
+    // kernel forms tried: blocks of 8 and 12 warps (14 and 16 for one grid
+    // under the projection closure), and for FP32 storage under the projection
+    // closure the 8-, 12- (and for one grid 16-) warp forms with plain stores
     const bool ce = !c->batch && c->inst[0].p.closure == tslb::CL_CHAPMAN_ENSKOG;
     struct Form {
         int nw;
         bool plain;
     };
     std::vector<Form> forms = {{8, false}, {12, false}};
-    if (!ce && !c->batch) forms.push_back({16, false});
+    if (!ce && !c->batch) {
+        forms.push_back({14, false});
+        forms.push_back({16, false});
+    }
     if (!ce && c->storage == TSLB_FP32) {
         forms.push_back({8, true});
         forms.push_back({12, true});
+        if (!c->batch) forms.push_back({16, true});
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event create");

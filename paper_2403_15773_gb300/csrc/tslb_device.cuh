@@ -189,6 +189,71 @@ __device__ __forceinline__ void bulk_wait() {
     asm volatile("cp.async.bulk.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ------------------------------------------ tensor memory (tcgen05, sm_100+)
+//
+// The step kernels of 14 and 16 warps keep per-thread state of the z march in
+// tensor memory (TMEM) instead of registers between planes: the block
+// allocates TMEM columns once, each warp reaches the 32 TMEM lanes of its
+// quarter (warp w: lanes 32 (w % 4) .. 32 (w % 4) + 31) through 32x32b
+// loads and stores (thread t of the warp <-> lane 32 (w % 4) + t, one 32-bit
+// value per column), and the block frees the columns before it exits.
+
+// Allocates ncols TMEM columns (a power of two >= 32) for the block; the
+// column address is written to *dst (shared memory).  All threads of one warp.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+// Frees the columns of tmem_alloc.  All threads of the allocating warp, after
+// every TMEM access of the block has completed.
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// Orders TMEM operations before / after a thread synchronisation (bar.sync).
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// Eight consecutive columns of this thread's lane, from / to registers.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr), "f"(v[0]),
+        "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+// Waits for this thread's TMEM loads; the loaded registers are operands so
+// that no use of them is placed before the wait.
+__device__ __forceinline__ void tmem_wait_ld(float (&v)[40]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
+                   "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19])
+                 :
+                 : "memory");
+    asm volatile(""
+                 : "+f"(v[20]), "+f"(v[21]), "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]),
+                   "+f"(v[27]), "+f"(v[28]), "+f"(v[29]), "+f"(v[30]), "+f"(v[31]), "+f"(v[32]), "+f"(v[33]),
+                   "+f"(v[34]), "+f"(v[35]), "+f"(v[36]), "+f"(v[37]), "+f"(v[38]), "+f"(v[39])
+                 :
+                 : "memory");
+}
+// Waits for this thread's TMEM stores (their source registers may then be reused).
+__device__ __forceinline__ void tmem_wait_st(const float (&v)[40]) {
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::"f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]),
+                 "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]),
+                 "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]), "f"(v[19])
+                 : "memory");
+    asm volatile("" ::"f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]),
+                 "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31]), "f"(v[32]), "f"(v[33]), "f"(v[34]),
+                 "f"(v[35]), "f"(v[36]), "f"(v[37]), "f"(v[38]), "f"(v[39])
+                 : "memory");
+}
+
 // Stored <-> FP32 conversion of one field value.
 template <typename S>
 struct Io;

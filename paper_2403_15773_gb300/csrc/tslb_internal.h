@@ -45,7 +45,7 @@ struct StepParams {
     int* err;                // set to 1 by a kernel whose bounded wait for its tile data gave up
     int test_stall;          // testing: TMA tiles expect bytes no copy delivers, in their first
                              // loads (1) or in the first loads of the march (2): the wait expires
-    int plain_stores;        // FP32, 8 or 12 warps: plain stores instead of the staging box + TMA store
+    int plain_stores;        // FP32, 8, 12 or 16 warps: plain stores instead of the staging box + TMA store
 };
 
 // Tensor maps of one step for the TMA tile copies of the step kernel: the 10

@@ -74,8 +74,10 @@ struct Step2Smem {
     // (finished planes leave by TMA store; 16-bit storage uses plain stores)
     static constexpr bool kFp32 = sizeof(S) == 4;
     static constexpr int TXS = TX;
-    // (16-warp blocks have no room for the staging boxes: plain stores)
-    static constexpr bool kTmaStore = kFp32 && NW <= 12 && ST;
+    static constexpr bool kTmaStore = kFp32 && ST;
+    // blocks of more than 12 warps keep the carries of the z march in tensor
+    // memory between planes (registers: 65536 / threads)
+    static constexpr bool TC = NW > 12;
     // box columns: staged columns x0-1 .. x0+30 (moments) and x0-2 .. x0+31
     // (phase field) from the 16-byte boundary below them
     static constexpr int MW = kFp32 ? 36 : 40;
@@ -104,16 +106,35 @@ struct Step2Smem {
     static constexpr size_t MOM = 0;                                 // [MS] moment boxes
     static constexpr size_t RING = MOM + MS * MOM_SLOT;              // [PS] phase-field boxes
     static constexpr int EPT = (NPH + NT - 1) / NT;                  // phase-field elements per thread
-    static constexpr size_t ZC = RING + PS * PHI_SLOT;               // [2][EPT * NT] float4 z combinations
-    static constexpr size_t YX = ZC + 2 * 16 * (size_t)EPT * NT;     // [20][NT] float y exchange
+    static constexpr size_t ZC = RING + PS * PHI_SLOT;               // [ZCN][EPT * NT] float4 z combinations
+    static constexpr size_t ZC_BUF = 16 * (size_t)EPT * NT;
     static constexpr size_t OUT_BOX = kTmaStore ? sizeof(float) * NFIELDS * TY * TXS : 0;  // [11][TY][TXS]
     static constexpr size_t OUT_SLOT = r128(OUT_BOX);
-    static constexpr size_t OUT = r128(YX + sizeof(float) * 20 * NT);  // [2] output staging boxes
-    static constexpr size_t BAR = OUT + 2 * OUT_SLOT;                 // NB mbarriers
-    static constexpr size_t BYTES = BAR + NB * sizeof(uint64_t) + 128;  // + alignment slack of the base
+    // bytes for zcn z-combination buffers and outn output staging boxes
+    static constexpr size_t bytes_for(int zcn, int outn) {
+        return r128(ZC + zcn * ZC_BUF + sizeof(float) * 20 * NT) + outn * OUT_SLOT + NB * sizeof(uint64_t) + 16 +
+               128;  // mbarriers, the TMEM address, alignment slack of the base
+    }
+    static constexpr size_t kMax = 227 * 1024;
+    // Two z-combination buffers let the next plane's combinations be formed
+    // amid the collision of this one, two staging boxes let a plane's TMA
+    // store overlap the next plane; where shared memory is short, one of each
+    // (the combinations are then formed after the plane's last reads of them,
+    // the store has the collision phase to finish reading its box).
+    static constexpr int ZCN = bytes_for(2, 2) <= kMax || bytes_for(2, 1) <= kMax ? 2 : 1;
+    static constexpr int OUTN = bytes_for(ZCN, 2) <= kMax ? 2 : 1;
+    static constexpr size_t YX = ZC + ZCN * ZC_BUF;                   // [20][NT] float y exchange
+    static constexpr size_t OUT = r128(YX + sizeof(float) * 20 * NT);  // [OUTN] output staging boxes
+    static constexpr size_t BAR = OUT + OUTN * OUT_SLOT;              // NB mbarriers
+    static constexpr size_t TMA_ADDR = BAR + NB * sizeof(uint64_t);   // TMEM column address (TC)
+    static constexpr size_t BYTES = TMA_ADDR + 16 + 128;              // + alignment slack of the base
+    // TMEM: 64 columns per warp for the 40 carries, four warps per lane quarter
+    static constexpr uint32_t TM_COLS = 256;
     static_assert(MAXOFFM + 32 <= MW && MAXOFFP + PHX <= PW, "box too narrow for the aligned tile");
     static_assert(!kTmaStore || (TXS * sizeof(S)) % 16 == 0, "store box rows must be 16-byte multiples");
-    static_assert(BYTES <= 227 * 1024, "more shared memory than a block can have");
+    static_assert(BYTES == bytes_for(ZCN, OUTN), "layout");
+    static_assert(BYTES <= kMax, "more shared memory than a block can have");
+    static_assert(!TC || NW <= 16, "TMEM: at most four warps share a lane quarter");
 };
 
 // The dynamic shared memory base rounded up to 128 bytes (TMA boxes).  The
@@ -147,6 +168,9 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     auto mslot = [](int q) { return (q + 12) % MS; };
     auto pslot = [](int q) { return (q + 20) % PS; };
     auto bslot = [](int i) { return (i + 12) % (PF + 1); };
+    // z-combination buffer of plane q, output staging box of plane q
+    auto zbuf = [](int q) { return L::ZCN == 2 ? ((q + 8) & 1) : 0; };
+    auto obuf = [](int q) { return L::OUTN == 2 ? ((q + 8) & 1) : 0; };
     constexpr int BPRO = PF + 1;  // mbarrier of the prologue loads
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* const sm = align128(smem_raw);
@@ -285,7 +309,20 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             if (inlet_planes) phib[e] = inlet_phi(P, psx, psy);
         }
     }
+    // TMEM for the z-march carries (blocks of more than 12 warps): warp 0
+    // allocates the block's columns; each warp uses 64 columns of its lane quarter
+    [[maybe_unused]] uint32_t tm_base = 0, tm_addr = 0;
+    [[maybe_unused]] uint32_t* const tm_slot = reinterpret_cast<uint32_t*>(sm + L::TMA_ADDR);
+    if constexpr (L::TC) {
+        if (w == 0) tmem_alloc(tm_slot, L::TM_COLS);
+        tmem_fence_before();
+    }
     const bool tma = __syncthreads_and(use_maps && inbox && (!WR || !(wrx || wry) || maps->wrap)) != 0;
+    if constexpr (L::TC) {
+        tmem_fence_after();
+        tm_base = *tm_slot;
+        tm_addr = tm_base + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(w >> 2) * 64u;
+    }
     if (tma) {
         if constexpr (!WR) {  // (WR: mrdA / mrdB set above)
             mrdA = resA;
@@ -437,7 +474,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             const float b = ic ? phib[e] : Io<S>::cvt(pc[prd[e]], inv);
             const float c = Io<S>::cvt(pp[prd[e]], inv);
             const float s = c + a;
-            zc[((q + 8) & 1) * (EPT * NT) + tid + e * NT] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
+            zc[zbuf(q) * (EPT * NT) + tid + e * NT] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
         }
     };
 
@@ -494,6 +531,41 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     for (int k = 0; k < 3; ++k) cPP[k] = cZ[k] = bc(0.f);
     float2 cAph = bc(0.f), cVP = bc(0.f);
     float sum_rho = 0.f, sum_phi = 0.f;
+    // TMEM form: the 34 carry values (40 columns) of each thread live in its
+    // TMEM lane between planes; (e) loads them, advances them and stores them
+    [[maybe_unused]] auto carries_pack = [&](float (&c)[40]) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            c[2 * k] = cPP[k].x, c[2 * k + 1] = cPP[k].y;
+            c[6 + 2 * k] = cZ[k].x, c[7 + 2 * k] = cZ[k].y;
+            c[24 + 2 * k] = cA[3 + k].x, c[25 + 2 * k] = cA[3 + k].y;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) c[12 + 2 * k] = cP[k].x, c[13 + 2 * k] = cP[k].y;
+        c[30] = cAph.x, c[31] = cAph.y, c[32] = cVP.x, c[33] = cVP.y;
+#pragma unroll
+        for (int k = 34; k < 40; ++k) c[k] = 0.f;
+    };
+    [[maybe_unused]] auto carries_unpack = [&](const float (&c)[40]) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            cPP[k] = make_float2(c[2 * k], c[2 * k + 1]);
+            cZ[k] = make_float2(c[6 + 2 * k], c[7 + 2 * k]);
+            cA[3 + k] = make_float2(c[24 + 2 * k], c[25 + 2 * k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cP[k] = make_float2(c[12 + 2 * k], c[13 + 2 * k]);
+        cAph = make_float2(c[30], c[31]);
+        cVP = make_float2(c[32], c[33]);
+    };
+    [[maybe_unused]] auto carries_store = [&]() {
+        float c[40];
+        carries_pack(c);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) tmem_st8(tm_addr + 8u * k, c + 8 * k);
+        tmem_wait_st(c);
+    };
+    if constexpr (L::TC) carries_store();
 
     const float om1 = 1.f - P.omega, fo = 1.f - 0.5f * P.omega;
     const float sig_half = -0.5f * P.sigma;
@@ -520,7 +592,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         resolve_axis(i, nz, P.face[4], P.face[5], sgz_cur, inl_cur);
         // plane i - 2 was staged by the previous iteration (and fenced): store it
         if (tst && tid == 0 && i >= z0 + 2) {
-            tma_store_4d(&maps->out, outb + ((i - 2 + 8) & 1) * OSL, x0, y0, i - 2, 0);
+            tma_store_4d(&maps->out, outb + obuf(i - 2) * OSL, x0, y0, i - 2, 0);
             bulk_commit();
         }
         const bool do_m = i + PF <= z1, do_p = i + 2 + PF <= z1 + 1;
@@ -560,7 +632,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
 
             // interface terms from the z combinations of phi at plane i
             float2 phi, Fx, Fy, Fz, nxv, nyv, nzv;
-            const float4* zci = zc + ((i + 8) & 1) * (EPT * NT);
+            const float4* zci = zc + zbuf(i) * (EPT * NT);
             static_assert(TX <= 28, "the interface stencil takes columns from the spare lanes 30, 31");
             interface4<NPH>(zci, lane, w, sig_half, P.normal_eps2, phi, Fx, Fy, Fz, nxv, nyv, nzv);
             if (inl_cur) {
@@ -569,7 +641,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             }
             // shared-memory work of the next plane amid the arithmetic of this one
             // (16-warp blocks, at 128 registers, do it in (e): here it spills)
-            if constexpr (NW <= 12) {
+            if constexpr (L::ZCN == 2) {
                 if (i < z1) zcombine(i + 1);
             }
 
@@ -633,7 +705,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                 }
         }
         // (e) below rewrites the staging box of plane i - 3: its store has read it
-        if (tst && tid == 0) bulk_wait_read<1>();
+        if (tst && tid == 0) bulk_wait_read<L::OUTN - 1>();
         __syncthreads();
 
         // (e) plane i: y shift and moments, z shift and moments, output of plane i - 1
@@ -655,6 +727,13 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                 }
             const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], h_dyB) + make_float2(h_dyA, ynext[19 * NT]), h_hx);
 
+            if constexpr (L::TC) {
+                float c[40];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) tmem_ld8(tm_addr + 8u * k, c + 8 * k);
+                tmem_wait_ld(c);
+                carries_unpack(c);
+            }
             const int gqx[6] = {0, 1, 0, 2, 0, 1}, gqy[6] = {0, 0, 1, 0, 2, 1};
             float2 O0[6], O1[6], O2[6];
 #pragma unroll
@@ -675,6 +754,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             const float2 phin = mad(0.125f, h_vzm, cAph);
             cAph = mad(0.125f, cVP, hxy);
             cVP = h_vzp;
+            if constexpr (L::TC) carries_store();
 
             if (i >= z0 + 1) {  // (every lane computes; halo and out-of-grid lanes do not write)
                 const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
@@ -696,7 +776,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                 val[F_PHI] = phin;
                 const long long zo = nxy * (i - 1);
                 if (tst) {  // into the staging box of plane i - 1: [field][tile row][tile column]
-                    float* ob = outb + ((i - 1 + 8) & 1) * OSL + (2 * w - 1) * TX + (lane - 1);
+                    float* ob = outb + obuf(i - 1) * OSL + (2 * w - 1) * TX + (lane - 1);
                     if (storeA) {
 #pragma unroll
                         for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX] = val[f].x;
@@ -741,16 +821,21 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         }
 
         if (tst) fence_proxy_async();  // the staging box is read by the TMA store next iteration
-        if constexpr (NW > 12) {
+        if constexpr (L::ZCN == 1) {
             if (i < z1) zcombine(i + 1);
         }
         commit(do_p, i + 2 + PF, do_m, i + PF);
     }
     // the last plane (z1 - 1) waits in its staging box
+    if constexpr (L::TC) tmem_fence_before();
     __syncthreads();
+    if constexpr (L::TC) {  // every TMEM access of the block has completed: release the columns
+        tmem_fence_after();
+        if (w == 0) tmem_dealloc(tm_base, L::TM_COLS);
+    }
     if (tst && tid == 0) {
         if (!dead) {
-            tma_store_4d(&maps->out, outb + ((z1 - 1 + 8) & 1) * OSL, x0, y0, z1 - 1, 0);
+            tma_store_4d(&maps->out, outb + obuf(z1 - 1) * OSL, x0, y0, z1 - 1, 0);
             bulk_commit();
         }
         bulk_wait<0>();
@@ -981,10 +1066,12 @@ cudaError_t launch_step_t(const StepParams& p, int st, const void* in, void* out
                               : launch_nw<12, S, true, true>(p, st, in, out, t_in, t_out, partials, s, m);
             if (pl) return launch_nw<12, S, false, false>(p, st, in, out, t_in, t_out, partials, s, m);
         }
+        if (p.block_warps == 16 && pl) return launch_nw<16, S, false, false>(p, st, in, out, t_in, t_out, partials, s, m);
     }
     switch (p.block_warps) {
         case 8: return launch_nw<8, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
         case 12: return launch_nw<12, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 14: return launch_nw<14, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
         case 16: return launch_nw<16, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
         default: return cudaErrorInvalidValue;
     }
@@ -1009,10 +1096,12 @@ template <typename S>
 cudaError_t prepare_t() {
     cudaError_t e = prepare_nw<8, S, true, false>();
     if (e == cudaSuccess) e = prepare_nw<12, S, true, false>();
+    if (e == cudaSuccess) e = prepare_nw<14, S, true, false>();
     if (e == cudaSuccess) e = prepare_nw<16, S, true, false>();
     if constexpr (sizeof(S) == 4) {
         if (e == cudaSuccess) e = prepare_nw<8, S, false, false>();
         if (e == cudaSuccess) e = prepare_nw<12, S, false, false>();
+        if (e == cudaSuccess) e = prepare_nw<16, S, false, false>();
         if (e == cudaSuccess) e = prepare_nw<8, S, true, true>();
         if (e == cudaSuccess) e = prepare_nw<12, S, true, true>();
         if (e == cudaSuccess) e = prepare_nw<8, S, false, true>();
@@ -1069,9 +1158,11 @@ template <typename S>
 size_t step_smem_bytes_t(int nw, bool plain) {
     if (sizeof(S) == 4 && plain && nw == 8) return Step2Smem<8, S, false>::BYTES;
     if (sizeof(S) == 4 && plain && nw == 12) return Step2Smem<12, S, false>::BYTES;
+    if (sizeof(S) == 4 && plain && nw == 16) return Step2Smem<16, S, false>::BYTES;
     switch (nw) {
         case 8: return Step2Smem<8, S>::BYTES;
         case 12: return Step2Smem<12, S>::BYTES;
+        case 14: return Step2Smem<14, S>::BYTES;
         default: return Step2Smem<16, S>::BYTES;
     }
 }
@@ -1192,10 +1283,10 @@ cudaError_t make_maps_t(const StepParams& p, const void* buf, const void* obuf, 
 cudaError_t make_tile_maps(const StepParams& p, int storage, const void* buf, const void* obuf, TileMaps* maps) {
     memset(maps, 0, sizeof(*maps));
     const size_t es = storage == ST_FP32 ? 4 : 2;
-    // TMA needs 16-byte aligned row pitches and bases; box sizes exist for 8, 12 and 16 warps
+    // TMA needs 16-byte aligned row pitches and bases; box sizes exist for 8, 12, 14 and 16 warps
     if (p.closure != CL_PROJECTION || ((size_t)p.nx * es) % 16 != 0 ||
         (reinterpret_cast<uintptr_t>(buf) % 16) != 0 ||
-        (p.block_warps != 8 && p.block_warps != 12 && p.block_warps != 16))
+        (p.block_warps != 8 && p.block_warps != 12 && p.block_warps != 14 && p.block_warps != 16))
         return cudaSuccess;
     return storage == ST_FP32 ? make_maps_t<float>(p, buf, obuf, maps) : make_maps_t<__half>(p, buf, obuf, maps);
 }

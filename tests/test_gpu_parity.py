@@ -144,7 +144,7 @@ def test_ragged_tiles_mixed_faces():
     check_parity(w, 100, fields=(rho0, u0, phi), pi=pi0)
 
 
-@pytest.mark.parametrize("block_warps", [8, 12, 16])
+@pytest.mark.parametrize("block_warps", [8, 12, 14, 16])
 def test_periodic_box_rows_droplet(block_warps):
     """A periodic droplet on a grid whose rows are 16-byte aligned (48 x 44 x
     40): tiles at the periodic faces take the sources of their wrapped ghosts
@@ -177,7 +177,7 @@ def test_periodic_box_rows_mixed_faces():
     check_parity(w, 60, fields=(rho0, u0, phi), pi=pi0)
 
 
-@pytest.mark.parametrize("tile_z,block_warps", [(5, 8), (0, 12), (9, 16)])
+@pytest.mark.parametrize("tile_z,block_warps", [(5, 8), (0, 12), (11, 14), (9, 16)])
 def test_periodic_jet_independent_of_tiling(tile_z, block_warps):
     """A jet with periodic sides on an aligned grid: bitwise the same fields for
     every tiling (side boxes at different tiles, element-wise 16-warp tiles)."""
@@ -235,7 +235,8 @@ def test_deterministic_and_graph_equals_plain_launches():
     assert sa == sb == sc
 
 
-@pytest.mark.parametrize("tile_z,block_warps", [(1, 0), (5, 0), (13, 0), (0, 8), (0, 12), (0, 16), (7, 16)])
+@pytest.mark.parametrize("tile_z,block_warps", [(1, 0), (5, 0), (13, 0), (0, 8), (0, 12), (0, 14), (6, 14),
+                                                 (0, 16), (7, 16)])
 def test_fields_independent_of_tiling(tile_z, block_warps):
     """Every node's arithmetic is the same whatever tile it falls in: the fields
     are bitwise identical for all slab depths and block shapes."""
