@@ -69,7 +69,10 @@ typedef enum {
     TSLB_BC_INLET = 1,     /* jet inlet: ghost with rho and P of the adjacent fluid node and
                               imposed u, phi (non-equilibrium extrapolation, Eq. original_neq) */
     TSLB_BC_OUTFLOW = 2,   /* zero-gradient copy of the adjacent fluid node */
-    TSLB_BC_FREE_SLIP = 3  /* specular mirror about the half-way plane */
+    TSLB_BC_FREE_SLIP = 3, /* specular mirror about the half-way plane */
+    TSLB_BC_HALO = 4       /* z faces only: the face borders a neighbouring slab of a domain split
+                              along z; the ghost planes beyond it (moments of one plane, phi of
+                              two) are written by tslb_halo_unpack before each step */
 } tslb_bc;
 
 typedef struct {
@@ -151,7 +154,8 @@ TSLB_API void tslb_default_options(tslb_options* opt);
 
 /* Bytes of device workspace tslb_init needs for this grid and options (the two
  * state buffers, the per-block FP64 partial sums and a few counters), or 0 if
- * the arguments are invalid. */
+ * the arguments are invalid.  The size holds the ghost planes of halo z faces,
+ * so it serves every boundary specification. */
 TSLB_API size_t tslb_workspace_bytes(const tslb_grid* grid, const tslb_options* opt);
 
 /* Creates a context on the current CUDA device.
@@ -289,6 +293,32 @@ TSLB_API tslb_status tslb_autotune(tslb_ctx* ctx, int32_t steps_per_trial, int32
  * Returns TSLB_ERR_CUDA if a launch fails; messages via tslb_last_error(NULL). */
 TSLB_API tslb_status tslb_field_sums_noalloc(const float* rho, const float* phi, int64_t n,
                                              double* out, void* cuda_stream);
+
+/* ---- Slabs of a domain split along z (multi-GPU decomposition). ----
+ *
+ * The paper runs one GPU and names multi-GPU runs as future work (Sec. 4
+ * and 5); the update reaches one node (moments) and two nodes (phi, for its
+ * stencils) beyond a plane, so a domain split into z slabs needs, before
+ * every step, one plane of the ten moment fields and two planes of phi from
+ * each neighbouring slab.  A slab is a single-grid context (projection
+ * closure, fused scheme) whose z faces toward its neighbours have the
+ * TSLB_BC_HALO rule; its other faces keep the global rules (the inlet on the
+ * first slab, the outflow on the last).  Per step: tslb_halo_pack on each
+ * slab, exchange the messages, tslb_halo_unpack, tslb_step(ctx, 1).
+ *
+ * A message is tslb_halo_values() values of the storage type: the ten
+ * moment fields (rho - 1, u, P, in the stored form) of one plane, nx*ny each,
+ * then phi of two planes in increasing z.  Side 0 is the -z side, 1 the +z
+ * side.  tslb_halo_pack(side) writes what the neighbour on that side needs
+ * (side 0: moments of plane 0, phi of planes 0, 1; side 1: plane nz - 1,
+ * planes nz - 2, nz - 1); tslb_halo_unpack(side) stores a message from the
+ * neighbour on that side into the ghost planes (the face must have the halo
+ * rule).  Both are asynchronous on the context stream for device buffers and
+ * synchronise for host buffers; the ghost planes are zero after
+ * tslb_set_state.  0 for a batch context. */
+TSLB_API size_t tslb_halo_values(const tslb_ctx* ctx);
+TSLB_API tslb_status tslb_halo_pack(tslb_ctx* ctx, int32_t side, void* dst, int on_device);
+TSLB_API tslb_status tslb_halo_unpack(tslb_ctx* ctx, int32_t side, const void* src, int on_device);
 
 /* Measurement helper (the paper has no counterpart): the FP32 fused
  * multiply-add rate of the current device, the arithmetic roofline of the

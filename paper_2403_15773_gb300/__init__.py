@@ -29,8 +29,8 @@ __all__ = [
     "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
     "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
     "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
-    "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate", "Simulation", "BatchSimulation",
-    "SYMBOLS",
+    "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate", "tslb_halo_values", "tslb_halo_pack",
+    "tslb_halo_unpack", "Simulation", "BatchSimulation", "SYMBOLS",
 ]
 
 TSLB_OK, TSLB_ERR_INVALID_ARG, TSLB_ERR_OOM, TSLB_ERR_CUDA, TSLB_ERR_UNSTABLE, TSLB_ERR_TIMEOUT, \
@@ -38,7 +38,7 @@ TSLB_OK, TSLB_ERR_INVALID_ARG, TSLB_ERR_OOM, TSLB_ERR_CUDA, TSLB_ERR_UNSTABLE, T
 TSLB_LATTICE_D3Q27_D3Q7 = 0
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 CLOSURES = {"projection": 0, "chapman_enskog": 1}
-FACES = {"periodic": 0, "inlet": 1, "outflow": 2, "free_slip": 3}
+FACES = {"periodic": 0, "inlet": 1, "outflow": 2, "free_slip": 3, "halo": 4}
 
 SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_set_state", "tslb_step",
            "tslb_get_moments", "tslb_get_phi", "tslb_sums", "tslb_get_time", "tslb_state_bytes",
@@ -46,7 +46,8 @@ SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_se
            "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
            "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
            "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
-           "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate")
+           "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate", "tslb_halo_values",
+           "tslb_halo_pack", "tslb_halo_unpack")
 
 
 class Grid(ctypes.Structure):
@@ -134,6 +135,12 @@ def lib() -> ctypes.CDLL:
             L.tslb_reset_averages.restype = ctypes.c_int
             L.tslb_fp32_lane_rate.argtypes = [ctypes.c_int32, VP, P(ctypes.c_double)]
             L.tslb_fp32_lane_rate.restype = ctypes.c_int
+            L.tslb_halo_values.argtypes = [VP]
+            L.tslb_halo_values.restype = ctypes.c_size_t
+            L.tslb_halo_pack.argtypes = [VP, ctypes.c_int32, VP, ctypes.c_int]
+            L.tslb_halo_pack.restype = ctypes.c_int
+            L.tslb_halo_unpack.argtypes = [VP, ctypes.c_int32, VP, ctypes.c_int]
+            L.tslb_halo_unpack.restype = ctypes.c_int
             for name in ("tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments", "tslb_batch_get_phi",
                          "tslb_batch_sums", "tslb_autotune"):
                 getattr(L, name).restype = ctypes.c_int
@@ -300,6 +307,18 @@ def tslb_get_averages(ctx: int, i: int, phi_sum: int, uz_sum: int, on_device: in
 
 def tslb_reset_averages(ctx: int):
     _check(lib().tslb_reset_averages(ctx), ctx)
+
+
+def tslb_halo_values(ctx: int) -> int:
+    return int(lib().tslb_halo_values(ctx))
+
+
+def tslb_halo_pack(ctx: int, side: int, dst: int, on_device: int):
+    _check(lib().tslb_halo_pack(ctx, int(side), dst, int(on_device)), ctx)
+
+
+def tslb_halo_unpack(ctx: int, side: int, src: int, on_device: int):
+    _check(lib().tslb_halo_unpack(ctx, int(side), src, int(on_device)), ctx)
 
 
 def tslb_fp32_lane_rate(packed: int, stream: int = 0) -> float:

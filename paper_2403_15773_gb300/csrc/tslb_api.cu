@@ -121,8 +121,12 @@ bool valid_grid(const tslb_grid* g, const int face[6], std::string& why) {
     const int n[3] = {g->nx, g->ny, g->nz};
     for (int a = 0; a < 3; ++a) {
         const int lo = face[2 * a], hi = face[2 * a + 1];
-        if (lo < 0 || lo > 3 || hi < 0 || hi > 3) {
+        if (lo < 0 || lo > 4 || hi < 0 || hi > 4) {
             why = "unknown face rule";
+            return false;
+        }
+        if (a < 2 && (lo == TSLB_BC_HALO || hi == TSLB_BC_HALO)) {
+            why = "the halo rule is only supported on the z faces";
             return false;
         }
         if ((lo == TSLB_BC_PERIODIC) != (hi == TSLB_BC_PERIODIC)) {
@@ -222,7 +226,8 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     p.tile_z = opt->tile_z > 0 ? (opt->tile_z < grid->nz ? opt->tile_z : grid->nz)
                                : auto_tile_z(grid, p.block_warps, default_tile_width(opt), device_sms());
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
-    p.fstride = (N + 63) / 64 * 64;
+    const long long halo = tslb::has_halo(p.face) ? (long long)tslb::kHaloPlanes * grid->nx * grid->ny : 0;
+    p.fstride = (N + halo + 63) / 64 * 64;
     p.omega = (float)omega;
     p.sigma = (float)sigma;
     p.gamma = 1.f / opt->interface_width;
@@ -543,6 +548,12 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
         g_init_err = "the Chapman-Enskog closure runs single grids with the fused scheme";
         return TSLB_ERR_INVALID_ARG;
     }
+    for (int i = 0; i < count && bcs; ++i)
+        if ((bcs[i].face[4] == TSLB_BC_HALO || bcs[i].face[5] == TSLB_BC_HALO) &&
+            (batch || o.scheme != 0 || o.closure != TSLB_CLOSURE_PROJECTION)) {
+            g_init_err = "halo faces (slabs of a z-split domain) run single grids, fused scheme, projection closure";
+            return TSLB_ERR_INVALID_ARG;
+        }
     std::vector<StepParams> ps(count);
     for (int i = 0; i < count; ++i) {
         std::string why;
@@ -682,6 +693,14 @@ tslb_status set_state_of(tslb_ctx* c, int i, const float* rho, const float* u, c
            "zero P");
     }
     if ((s = put_field(c, I, phi, tslb::F_PHI, on_device)) != TSLB_OK) return s;
+    if (tslb::has_halo(I.p.face)) {  // ghost planes of halo faces: zero until the first tslb_halo_unpack
+        const size_t nxy = (size_t)I.p.nx * I.p.ny;
+        char* b0 = static_cast<char*>(I.buf[c->cur]);
+        for (int f = 0; f < tslb::stored_fields(I.p.closure); ++f)
+            CK(cudaMemsetAsync(b0 + ((size_t)f * I.p.fstride + (size_t)N) * c->elem, 0,
+                               tslb::kHaloPlanes * nxy * c->elem, c->stream),
+               "zero ghost planes");
+    }
     if (I.avg) {
         CK(cudaMemsetAsync(I.avg, 0, 2 * (size_t)I.p.fstride * sizeof(double), c->stream), "clear averages");
         c->avg_steps = 0;
@@ -769,8 +788,12 @@ size_t tslb_batch_workspace_bytes(int32_t count, const tslb_grid* grids, const t
     std::vector<StepParams> ps(count);
     for (int i = 0; i < count; ++i) {
         std::string why;
-        // the face rules only affect validity, not the size: size with periodic faces
-        if (!make_params(&grids[i], 1.0, 0.0, &b, &o, ps[i], why)) return 0;
+        // The face rules affect the size only through halo z faces (four ghost
+        // planes per field): a single grid is sized for them (where its z axis
+        // allows them), a batch, which has none, with periodic faces.
+        tslb_boundary bi = b;
+        if (count == 1 && grids[i].nz >= 2) bi.face[4] = bi.face[5] = TSLB_BC_HALO;
+        if (!make_params(&grids[i], 1.0, 0.0, &bi, &o, ps[i], why)) return 0;
     }
     return layout_for(ps, elem_size(o.storage), o.storage, count > 1, o.average != 0, o.scheme).total;
 }
@@ -1150,6 +1173,61 @@ tslb_status tslb_reset_averages(tslb_ctx* c) {
         CK(cudaMemsetAsync(I.avg, 0, 2 * (size_t)I.p.fstride * sizeof(double), c->stream), "clear averages");
     CK(cudaStreamSynchronize(c->stream), "averages synchronise");
     c->avg_steps = 0;
+    return TSLB_OK;
+}
+
+size_t tslb_halo_values(const tslb_ctx* c) {
+    if (!c || c->batch) return 0;
+    return (size_t)(tslb::F_PHI + 2) * c->inst[0].p.nx * c->inst[0].p.ny;
+}
+
+tslb_status tslb_halo_pack(tslb_ctx* c, int32_t side, void* dst, int on_device) {
+    if (!c || !dst || (side != 0 && side != 1)) return TSLB_ERR_INVALID_ARG;
+    if (c->batch) return bad(c, "halo messages are per single-grid context");
+    Instance& I = c->inst[0];
+    if (!I.set) return bad(c, "no state", TSLB_ERR_STATE);
+    if (on_device && !is_device_ptr(dst)) return bad(c, "on_device pointers must be device memory");
+    CK(cudaSetDevice(c->device), "set device");
+    const size_t nxy = (size_t)I.p.nx * I.p.ny, e = c->elem;
+    // side 0: what the neighbour below needs (moments of plane 0, phi of planes 0, 1);
+    // side 1: what the neighbour above needs (plane nz - 1; planes nz - 2, nz - 1)
+    const size_t zm = side == 0 ? 0 : (size_t)I.p.nz - 1, zp = side == 0 ? 0 : (size_t)I.p.nz - 2;
+    const char* b = static_cast<const char*>(I.buf[c->cur]);
+    char* d = static_cast<char*>(dst);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpy2DAsync(d, nxy * e, b + zm * nxy * e, (size_t)I.p.fstride * e, nxy * e, tslb::F_PHI, kind,
+                         c->stream),
+       "halo pack (moments)");
+    CK(cudaMemcpyAsync(d + (size_t)tslb::F_PHI * nxy * e, b + ((size_t)tslb::F_PHI * I.p.fstride + zp * nxy) * e,
+                       2 * nxy * e, kind, c->stream),
+       "halo pack (phase field)");
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "halo pack synchronise");
+    return TSLB_OK;
+}
+
+tslb_status tslb_halo_unpack(tslb_ctx* c, int32_t side, const void* src, int on_device) {
+    if (!c || !src || (side != 0 && side != 1)) return TSLB_ERR_INVALID_ARG;
+    if (c->batch) return bad(c, "halo messages are per single-grid context");
+    Instance& I = c->inst[0];
+    if (!I.set) return bad(c, "no state", TSLB_ERR_STATE);
+    if (I.p.face[4 + side] != tslb::BC_HALO) return bad(c, "that z face does not have the halo rule");
+    if (on_device && !is_device_ptr(src)) return bad(c, "on_device pointers must be device memory");
+    CK(cudaSetDevice(c->device), "set device");
+    const size_t nxy = (size_t)I.p.nx * I.p.ny, e = c->elem, nz = (size_t)I.p.nz;
+    // side 0 (from the neighbour below): moments -> plane -1 (stored as nz + 3),
+    // phi -> planes -2, -1 (nz + 2, nz + 3); side 1 (from above): moments ->
+    // plane nz, phi -> planes nz, nz + 1
+    const size_t zm = side == 0 ? nz + 3 : nz, zp = side == 0 ? nz + 2 : nz;
+    char* b = static_cast<char*>(I.buf[c->cur]);
+    const char* sp = static_cast<const char*>(src);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpy2DAsync(b + zm * nxy * e, (size_t)I.p.fstride * e, sp, nxy * e, nxy * e, tslb::F_PHI, kind,
+                         c->stream),
+       "halo unpack (moments)");
+    CK(cudaMemcpyAsync(b + ((size_t)tslb::F_PHI * I.p.fstride + zp * nxy) * e, sp + (size_t)tslb::F_PHI * nxy * e,
+                       2 * nxy * e, kind, c->stream),
+       "halo unpack (phase field)");
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "halo unpack synchronise");
     return TSLB_OK;
 }
 

@@ -27,11 +27,14 @@ constexpr int PHX = 34;       // footprint columns of a tile: x0 - 2 .. x0 + 31
 // Source coordinate of grid coordinate g on an axis of n nodes whose lower /
 // upper faces follow rule lo / hi.  sign = -1 for a mirror image, inlet = 1
 // for the inlet ghost.  Coordinates farther out than any stencil reaches are
-// clamped into the grid (their values are never used).
+// clamped into the grid (their values are never used).  A HALO face (z only)
+// maps its ghost planes -2, -1 / n, n + 1 to the planes stored after the
+// interior (n + 2, n + 3 / n, n + 1).
 __device__ __forceinline__ int resolve_axis(int g, int n, int lo, int hi, float& sign, int& inlet) {
     sign = 1.f;
     if (g >= 0 && g < n) return g;
     const int kind = g < 0 ? lo : hi;
+    if (kind == BC_HALO) return g < 0 ? max(n + kHaloPlanes + g, n + 2) : min(g, n + 1);
     int s;
     if (kind == BC_PERIODIC) {
         s = g % n;

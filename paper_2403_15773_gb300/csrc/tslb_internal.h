@@ -8,7 +8,14 @@
 
 namespace tslb {
 
-enum { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTFLOW = 2, BC_FREE_SLIP = 3 };
+enum { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTFLOW = 2, BC_FREE_SLIP = 3, BC_HALO = 4 };
+// A z face with the HALO rule borders a neighbouring slab of a domain split
+// along z: the ghost planes beyond it hold the neighbour's stored fields,
+// written by the caller before each step.  A grid with a HALO face stores
+// four ghost planes after the interior of every field: planes nz, nz + 1
+// (above) and, at plane indices nz + 2, nz + 3, the planes -2, -1 (below).
+constexpr int kHaloPlanes = 4;
+inline __host__ __device__ bool has_halo(const int face[6]) { return face[4] == BC_HALO || face[5] == BC_HALO; }
 enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
 
 // Stored fields of one state buffer, each a block of `fstride` elements:

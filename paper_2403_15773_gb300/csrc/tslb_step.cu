@@ -1231,7 +1231,9 @@ cudaError_t make_maps_t(const StepParams& p, const void* buf, const void* obuf, 
     const CUtensorMapDataType dt = sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     EncodeTiled enc = encode_tiled();
     if (!enc) return cudaSuccess;  // valid stays 0: element-wise loads
-    const cuuint64_t dm[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz, 10};
+    // (a grid with a HALO face also stores its ghost planes after the interior)
+    const cuuint64_t nzs = (cuuint64_t)p.nz + (has_halo(p.face) ? kHaloPlanes : 0);
+    const cuuint64_t dm[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, nzs, 10};
     const cuuint64_t sm[3] = {p.nx * es, (cuuint64_t)p.nx * p.ny * es, (cuuint64_t)p.fstride * es};
     const cuuint32_t bm[4] = {(cuuint32_t)mw, (cuuint32_t)nr, 1, 10};
     const cuuint32_t one[4] = {1, 1, 1, 1};

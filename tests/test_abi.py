@@ -77,6 +77,8 @@ def _bc(faces):
     dict(faces=("periodic", "outflow", "periodic", "periodic", "periodic", "periodic")),
     dict(grid=(1, 8, 8), faces=("free_slip", "free_slip", "periodic", "periodic", "periodic", "periodic")),
     dict(grid=(8, 8, 0)),
+    dict(faces=("halo", "halo", "periodic", "periodic", "periodic", "periodic")),
+    dict(faces=("periodic", "periodic", "periodic", "periodic", "halo", "periodic")),
 ])
 def test_init_rejects_invalid_arguments_before_touching_the_gpu(case):
     g = tslb.Grid(*case.get("grid", (8, 8, 8)))
@@ -111,6 +113,31 @@ def test_kernel_options_are_checked_before_touching_the_gpu():
         with pytest.raises(tslb.TslbError) as ei:
             tslb.tslb_init(g, 1.5, 0.0, None, o)
         assert ei.value.status == tslb.TSLB_ERR_INVALID_ARG
+
+
+def test_halo_faces_need_the_fused_projection_step():
+    g = tslb.Grid(8, 8, 8)
+    bc = _bc(("periodic",) * 4 + ("halo", "outflow"))
+    for kw in (dict(closure=1), dict(scheme=1)):
+        o = tslb.tslb_default_options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        with pytest.raises(tslb.TslbError) as ei:
+            tslb.tslb_init(g, 1.5, 0.0, bc, o)
+        assert ei.value.status == tslb.TSLB_ERR_INVALID_ARG
+    with pytest.raises(tslb.TslbError):
+        tslb.tslb_init_batch([g], [1.5], [0.0], [bc])
+
+
+def test_workspace_holds_the_ghost_planes_of_halo_faces():
+    """A single grid's workspace is sized for halo z faces (four ghost planes
+    after each field of both state buffers), whatever faces it gets."""
+    g = tslb.Grid(16, 12, 10)
+    N, nxy = 16 * 12 * 10, 16 * 12
+    assert tslb.tslb_workspace_bytes(g) >= 2 * 11 * (N + 4 * nxy) * 4
+    o = tslb.tslb_default_options()
+    o.storage = tslb.STORAGE["fp16"]
+    assert tslb.tslb_workspace_bytes(g, o) >= 2 * 11 * (N + 4 * nxy) * 2
 
 
 def test_chapman_enskog_state_is_five_fields():
