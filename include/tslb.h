@@ -110,7 +110,9 @@ typedef struct {
     float interface_width;  /* W: anti-diffusion Gamma = 1/W gives a tanh(2x/W) interface; default 3 */
     float normal_eps;       /* the interface normal is grad phi / sqrt(|grad phi|^2 + eps^2); default 1e-2 */
     float field_scale[4];   /* 16-bit storage: stored value = scale * (rho - 1), scale * u,
-                               scale * P, scale * phi; 0 = default (1/(3 U^2), 1/(2 U), 1e3, 1) */
+                               scale * P, scale * d with d = phi -+ (1 + 1/16) the deviation of
+                               phi from the nearer of +-(1 + 1/16) (its sign tells which; |phi|
+                               saturates at 1 + 1/16); 0 = default (1/(3 U^2), 1/(2 U), 1e3, 1) */
     int32_t check_every;    /* tslb_step checks the FP64 sums for non-finite values every this
                                many steps (synchronises); 0 = never (default) */
     int32_t tile_z;         /* z extent of one thread block's slab; 0 = automatic (single grids: the

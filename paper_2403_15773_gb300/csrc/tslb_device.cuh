@@ -257,7 +257,27 @@ __device__ __forceinline__ void tmem_wait_st(const float (&v)[40]) {
                  : "memory");
 }
 
-// Stored <-> FP32 conversion of one field value.
+// Stored <-> FP32 conversion of one field value.  16-bit storage keeps
+// scaled deviations from the rest state (rho - 1, u, P and the phase field's
+// deviation below); FP32 storage keeps the values themselves.
+//
+// The phase field in 16-bit storage.  Its bulk values sit near +-1, where a
+// 16-bit float is coarsest (2^-11 in FP16, 2^-8 in BF16 below 1), and the
+// rounding of the bulk then moves the interfaces.  So it is stored as the
+// deviation from the nearer of +-(1 + m), m = 1/16:
+//   d = phi - (1 + m) for phi >= 0 (d < 0),  d = phi + (1 + m) for phi < 0 (d > 0),
+// which is small in the bulk (|d| ~ m, resolved to 2^-15 in FP16) and whose
+// sign tells the branch back: phi = d - copysign(1 + m, d).  The margin m
+// leaves room for the overshoot of +-1 the phase field shows at interfaces
+// (a few 10^-3); beyond it, |phi| would saturate at 1 + m (d rounds to -0 /
+// +0, which decode to +-(1 + m)).
+constexpr float kPhiOff = 1.f + 1.f / 16.f;
+__device__ __forceinline__ float phi_encode(float v) {
+    const float d = v - copysignf(kPhiOff, v);
+    return signbit(v) ? (d > 0.f ? d : 0.f) : (d < 0.f ? d : -0.f);
+}
+__device__ __forceinline__ float phi_decode(float d) { return d - copysignf(kPhiOff, d); }
+
 template <typename S>
 struct Io;
 template <>
@@ -268,6 +288,12 @@ struct Io<float> {
     static __device__ __forceinline__ float ld(const float* p, float) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
     static __device__ __forceinline__ float round_trip(float v, float, float) { return v; }
+    // the phase field (FP32: the value itself)
+    static __device__ __forceinline__ float from_raw_phi(unsigned short, float) { return 0.f; }
+    static __device__ __forceinline__ float cvt_phi(float v, float) { return v; }
+    static __device__ __forceinline__ float ld_phi(const float* p, float) { return __ldg(p); }
+    static __device__ __forceinline__ void st_phi(float* p, float v, float) { *p = v; }
+    static __device__ __forceinline__ float round_trip_phi(float v, float, float) { return v; }
 };
 template <>
 struct Io<__half> {
@@ -280,6 +306,15 @@ struct Io<__half> {
     static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
     static __device__ __forceinline__ float round_trip(float v, float s, float inv) {
         return __half2float(__float2half_rn(v * s)) * inv;
+    }
+    static __device__ __forceinline__ float from_raw_phi(unsigned short r, float inv) {
+        return phi_decode(from_raw(r, inv));
+    }
+    static __device__ __forceinline__ float cvt_phi(__half v, float inv) { return phi_decode(cvt(v, inv)); }
+    static __device__ __forceinline__ float ld_phi(const __half* p, float inv) { return phi_decode(ld(p, inv)); }
+    static __device__ __forceinline__ void st_phi(__half* p, float v, float s) { st(p, phi_encode(v), s); }
+    static __device__ __forceinline__ float round_trip_phi(float v, float s, float inv) {
+        return phi_decode(round_trip(phi_encode(v), s, inv));
     }
 };
 template <>
@@ -295,6 +330,17 @@ struct Io<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v, float s) { *p = __float2bfloat16_rn(v * s); }
     static __device__ __forceinline__ float round_trip(float v, float s, float inv) {
         return __bfloat162float(__float2bfloat16_rn(v * s)) * inv;
+    }
+    static __device__ __forceinline__ float from_raw_phi(unsigned short r, float inv) {
+        return phi_decode(from_raw(r, inv));
+    }
+    static __device__ __forceinline__ float cvt_phi(__nv_bfloat16 v, float inv) { return phi_decode(cvt(v, inv)); }
+    static __device__ __forceinline__ float ld_phi(const __nv_bfloat16* p, float inv) {
+        return phi_decode(ld(p, inv));
+    }
+    static __device__ __forceinline__ void st_phi(__nv_bfloat16* p, float v, float s) { st(p, phi_encode(v), s); }
+    static __device__ __forceinline__ float round_trip_phi(float v, float s, float inv) {
+        return phi_decode(round_trip(phi_encode(v), s, inv));
     }
 };
 

@@ -470,9 +470,9 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         // (elements beyond NPH read box position 0 and fill padding of zc)
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-            const float a = im ? phib[e] : Io<S>::cvt(pm[prd[e]], inv);
-            const float b = ic ? phib[e] : Io<S>::cvt(pc[prd[e]], inv);
-            const float c = Io<S>::cvt(pp[prd[e]], inv);
+            const float a = im ? phib[e] : Io<S>::cvt_phi(pm[prd[e]], inv);
+            const float b = ic ? phib[e] : Io<S>::cvt_phi(pc[prd[e]], inv);
+            const float c = Io<S>::cvt_phi(pp[prd[e]], inv);
             const float s = c + a;
             zc[zbuf(q) * (EPT * NT) + tid + e * NT] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
         }
@@ -789,21 +789,23 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                     if (storeA) {
                         S* o = out + zo + sxyA;
 #pragma unroll
-                        for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
+                        for (int f = 0; f < F_PHI; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
+                        Io<S>::st_phi(o + F_PHI * fs, val[F_PHI].x, P.scale[F_PHI]);
                     }
                     if (storeB) {
                         S* o = out + zo + sxyB;
 #pragma unroll
-                        for (int f = 0; f < NFIELDS; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
+                        for (int f = 0; f < F_PHI; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
+                        Io<S>::st_phi(o + F_PHI * fs, val[F_PHI].y, P.scale[F_PHI]);
                     }
                 }
                 if (storeA) {
                     sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                    sum_phi += Io<S>::round_trip(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                    sum_phi += Io<S>::round_trip_phi(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
                 if (storeB) {
                     sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                    sum_phi += Io<S>::round_trip(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                    sum_phi += Io<S>::round_trip_phi(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
                 if (P.avg) {  // time sums of the new phi and u_z (FP64)
                     if (storeA) {
@@ -973,7 +975,10 @@ __global__ void __launch_bounds__(CONV_THREADS) put_field_kernel(const __grid_co
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         const float v = src[i];
-        Io<S>::st(dst + i, field == F_DRHO ? v - 1.f : v, sc);
+        if (field == F_PHI)
+            Io<S>::st_phi(dst + i, v, sc);
+        else
+            Io<S>::st(dst + i, field == F_DRHO ? v - 1.f : v, sc);
     }
 }
 
@@ -986,7 +991,7 @@ __global__ void __launch_bounds__(CONV_THREADS) state_sums_kernel(const __grid_c
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         sr += Io<S>::ld(st + F_DRHO * fs + i, P.inv_scale[F_DRHO]);
-        sp += Io<S>::ld(st + field_slot(P.closure, F_PHI) * fs + i, P.inv_scale[F_PHI]);
+        sp += Io<S>::ld_phi(st + field_slot(P.closure, F_PHI) * fs + i, P.inv_scale[F_PHI]);
     }
     block_partials<S>(sr, sp, partials);
 }
@@ -1000,7 +1005,7 @@ __global__ void __launch_bounds__(CONV_THREADS) get_field_kernel(const __grid_co
     const float inv = P.inv_scale[field];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
-        const float v = Io<S>::ld(src + i, inv);
+        const float v = field == F_PHI ? Io<S>::ld_phi(src + i, inv) : Io<S>::ld(src + i, inv);
         dst[i] = field == F_DRHO ? 1.f + v : v;
     }
 }

@@ -155,7 +155,7 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
             for (int e = 0; e < EPT; ++e) {
                 const int idx = tid + e * NT;
                 if (idx < NPH) {
-                    if (!r_inl) dphi[idx] = Io<S>::from_raw(rphi[e], P.inv_scale[F_PHI]);
+                    if (!r_inl) dphi[idx] = Io<S>::from_raw_phi(rphi[e], P.inv_scale[F_PHI]);
                     to_j(dj, idx, e, Io<S>::from_raw(rj[0][e], P.inv_scale[F_DRHO]),
                          Io<S>::from_raw(rj[1][e], P.inv_scale[F_UX]), Io<S>::from_raw(rj[2][e], P.inv_scale[F_UY]),
                          Io<S>::from_raw(rj[3][e], P.inv_scale[F_UZ]), r_sgz, r_inl);
@@ -304,16 +304,18 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
                 if (storeA) {
                     S* o = out + zo + oA;
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[fld[f]]);
+                    for (int f = 0; f < 4; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[fld[f]]);
+                    Io<S>::st_phi(o + 4 * fs, val[4].x, P.scale[F_PHI]);
                     sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                    sum_phi += Io<S>::round_trip(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                    sum_phi += Io<S>::round_trip_phi(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
                 if (storeB) {
                     S* o = out + zo + oB;
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[fld[f]]);
+                    for (int f = 0; f < 4; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[fld[f]]);
+                    Io<S>::st_phi(o + 4 * fs, val[4].y, P.scale[F_PHI]);
                     sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                    sum_phi += Io<S>::round_trip(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                    sum_phi += Io<S>::round_trip_phi(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
                 if (P.avg) {  // time sums of the new phi and u_z (FP64)
                     if (storeA) {
