@@ -140,7 +140,8 @@ typedef struct {
                                same to the first loads of the plane march, so the tile gives up
                                with later loads still in flight (it lets them land before it
                                releases its barriers); 0 = off (default) */
-    int32_t plain_stores;   /* FP32 storage, blocks of 8, 12 or 16 warps: 1 = the step kernel writes each
+    int32_t plain_stores;   /* FP32 storage, blocks of 8, 12 or 16 warps (8 or 12 under the
+                               Chapman-Enskog closure): 1 = the step kernel writes each
                                finished plane with plain stores instead of staging it in shared
                                memory for one TMA store; the smaller shared-memory footprint leaves
                                the L1 cache more room for tiles that load element by element

@@ -407,8 +407,14 @@ cudaError_t launch_one(tslb_ctx* c, int q) {
     }
     if (!c->batch && c->inst[0].p.closure == tslb::CL_CHAPMAN_ENSKOG) {
         Instance& I = c->inst[0];
+        tslb::TileMaps& m = I.maps[q];
+        if (m.block_warps != I.p.block_warps) {  // the output box is shaped for one block size
+            cudaError_t e = tslb::make_tile_maps(I.p, c->storage, I.buf[q], I.buf[q ^ 1], &m);
+            if (e != cudaSuccess) return e;
+            m.block_warps = I.p.block_warps;
+        }
         return tslb::launch_step_ce(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
-                                    c->partials, c->stream);
+                                    c->partials, c->stream, &m);
     }
     if (!c->batch) {
         Instance& I = c->inst[0];
@@ -951,8 +957,8 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     CK(cudaSetDevice(c->device), "set device");
     const int q = c->cur;
     // kernel forms tried: blocks of 8 and 12 warps (14 and 16 for one grid
-    // under the projection closure), and for FP32 storage under the projection
-    // closure the 8-, 12- (and for one grid 16-) warp forms with plain stores
+    // under the projection closure), and for FP32 storage the 8-, 12- (and for
+    // one grid under the projection closure 16-) warp forms with plain stores
     const bool ce = !c->batch && c->inst[0].p.closure == tslb::CL_CHAPMAN_ENSKOG;
     struct Form {
         int nw;
@@ -963,10 +969,10 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
         forms.push_back({14, false});
         forms.push_back({16, false});
     }
-    if (!ce && c->storage == TSLB_FP32) {
+    if (c->storage == TSLB_FP32) {
         forms.push_back({8, true});
         forms.push_back({12, true});
-        if (!c->batch) forms.push_back({16, true});
+        if (!ce && !c->batch) forms.push_back({16, true});
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event create");

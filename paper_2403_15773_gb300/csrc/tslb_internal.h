@@ -113,8 +113,10 @@ cudaError_t prepare_kernels(int storage);
 
 // Step kernel of the Chapman-Enskog closure (tslb_step_ce.cu; FP32 or 16-bit
 // storage, blocks of 8 or 12 warps), same contract as launch_step.
+// maps: the output map of the 5 stored fields (staged TMA stores, FP32) or null.
 cudaError_t launch_step_ce(const StepParams& p, int storage, const void* in, void* out,
-                           const long long* t_in, long long* t_out, double* partials, cudaStream_t s);
+                           const long long* t_in, long long* t_out, double* partials, cudaStream_t s,
+                           const TileMaps* maps = nullptr);
 cudaError_t prepare_kernels_ce(int storage);
 
 // One caller field (float, device) -> one stored field (rho - 1 for F_DRHO).

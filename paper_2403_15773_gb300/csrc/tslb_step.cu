@@ -1287,9 +1287,35 @@ cudaError_t make_maps_t(const StepParams& p, const void* buf, const void* obuf, 
 }
 }  // namespace
 
+// Output map of the Chapman-Enskog step (FP32): the 5 stored fields of the
+// output buffer as {nx, ny, nz, 5}, boxes of [5][2 nw - 2 rows][28 columns].
+static cudaError_t make_ce_out_map(const StepParams& p, const void* obuf, TileMaps* m) {
+    EncodeTiled enc = encode_tiled();
+    if (!enc || !obuf || reinterpret_cast<uintptr_t>(obuf) % 16 != 0) return cudaSuccess;
+    const cuuint64_t es = sizeof(float);
+    const cuuint64_t dout[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz, 5};
+    const cuuint64_t sm[3] = {p.nx * es, (cuuint64_t)p.nx * p.ny * es, (cuuint64_t)p.fstride * es};
+    const cuuint32_t bo[4] = {(cuuint32_t)TX, (cuuint32_t)(2 * p.block_warps - 2), 1, 5};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    if (enc(&m->out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(obuf), dout, sm, bo, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+        m->store = 1;
+        m->block_warps = p.block_warps;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t make_tile_maps(const StepParams& p, int storage, const void* buf, const void* obuf, TileMaps* maps) {
     memset(maps, 0, sizeof(*maps));
     const size_t es = storage == ST_FP32 ? 4 : 2;
+    // the Chapman-Enskog step loads element by element; FP32 grids with
+    // 16-byte rows get its output map (staged TMA stores)
+    if (p.closure == CL_CHAPMAN_ENSKOG) {
+        if (storage != ST_FP32 || ((size_t)p.nx * es) % 16 != 0 || (p.block_warps != 8 && p.block_warps != 12))
+            return cudaSuccess;
+        return make_ce_out_map(p, obuf, maps);
+    }
     // TMA needs 16-byte aligned row pitches and bases; box sizes exist for 8, 12, 14 and 16 warps
     if (p.closure != CL_PROJECTION || ((size_t)p.nx * es) % 16 != 0 ||
         (reinterpret_cast<uintptr_t>(buf) % 16) != 0 ||

@@ -18,6 +18,8 @@
 //     combinations (d_x = D_x S'_y S'_z / 72 and its permutations);
 //   * only the moments rho, j are gathered after streaming: the sweeps carry
 //     the x moments 0 and 1 and the (x, y) moment pairs (0,0), (1,0), (0,1).
+#include <cstring>
+
 #include "tslb_device.cuh"
 
 namespace tslb {
@@ -36,15 +38,25 @@ struct StepCeSmem {
     static constexpr int YX = JZ2 + 4 * NPH;        // [2][14][NT] y exchange
     static constexpr int FLOATS = YX + 28 * NT;
     static constexpr size_t BYTES = sizeof(float) * FLOATS;
+    // FP32 form with staged stores: two output staging boxes [5][TY][TX] of
+    // finished planes that leave by TMA store (+ slack to align them to 128 B)
+    static constexpr int TY = NR - 2;
+    static constexpr int OUT_BOX = (5 * TY * TX + 31) / 32 * 32;  // box stride, a multiple of 128 bytes
+    static constexpr int OUT = FLOATS;
+    static constexpr size_t BYTES_ST = sizeof(float) * (OUT + 2 * OUT_BOX + 32);
     static_assert(JZ4 % 4 == 0 && JZ2 % 2 == 0, "vector slots must be aligned");
+    static_assert((TX * sizeof(float)) % 16 == 0, "store box rows must be 16-byte multiples");
+    static_assert(BYTES_ST <= 227 * 1024, "more shared memory than a block can have");
 };
 
 constexpr int PHI_SLOT = 4;  // buffer slot of phi under this closure
 
-template <int NW, typename S>
-__device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __restrict__ in, S* __restrict__ out,
-                                             const long long t, const int bx, const int by, const int bz,
-                                             double* __restrict__ part) {
+// ST: finished planes (FP32) are staged in shared memory and leave by one TMA
+// store per plane (maps->out, 5 fields), instead of plain stores.
+template <int NW, typename S, bool ST>
+__device__ __forceinline__ void step_tile_ce(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
+                                             S* __restrict__ out, const long long t, const int bx, const int by,
+                                             const int bz, double* __restrict__ part) {
     using L = StepCeSmem<NW>;
     constexpr int NT = L::NT, NR = L::NR, NPH = L::NPH;
     constexpr int TY = NR - 2;
@@ -56,6 +68,9 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
     float4* const jz4 = reinterpret_cast<float4*>(smem + L::JZ4);
     float2* const jz2 = reinterpret_cast<float2*>(smem + L::JZ2);
     float* const yx = smem + L::YX;
+    // (ST) the staging boxes, 128-byte aligned within the dynamic shared memory
+    [[maybe_unused]] float* const outb =
+        smem + L::OUT + ((0u - (unsigned)__cvta_generic_to_shared(smem + L::OUT)) & 127u) / sizeof(float);
 
     const int lane = threadIdx.x, w = threadIdx.y, tid = lane + 32 * w;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
@@ -254,6 +269,11 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
     //   (e) y / z stages of plane i - 1 (output of plane i - 2),
     //   (d) stencils, collision and x sweep of plane i.
     for (int i = z0 - 1; i <= z1 + 1; ++i) {
+        // plane i - 3 was staged two iterations ago (and fenced): store it
+        if (ST && tid == 0 && i >= z0 + 3) {
+            tma_store_4d(&maps->out, outb + ((i - 3 + 8) & 1) * L::OUT_BOX, x0, y0, i - 3, 0);
+            bulk_commit();
+        }
         issue(i + 3);
         cp_async_commit();
         cp_async_wait<1>();
@@ -301,19 +321,35 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
                 const float2 val[5] = {dr, ux, uy, uz, phin};
                 const int fld[5] = {F_DRHO, F_UX, F_UY, F_UZ, F_PHI};
                 const long long zo = nxy * (i - 2);
-                if (storeA) {
-                    S* o = out + zo + oA;
+                if constexpr (ST) {  // into the staging box of plane i - 2: [field][tile row][tile column]
+                    float* ob = outb + ((i - 2 + 8) & 1) * L::OUT_BOX + (2 * w - 1) * TX + (lane - 1);
+                    if (storeA) {
 #pragma unroll
-                    for (int f = 0; f < 4; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[fld[f]]);
-                    Io<S>::st_phi(o + 4 * fs, val[4].x, P.scale[F_PHI]);
+                        for (int f = 0; f < 5; ++f) ob[f * TY * TX] = val[f].x;
+                    }
+                    if (storeB) {
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) ob[f * TY * TX + TX] = val[f].y;
+                    }
+                } else {
+                    if (storeA) {
+                        S* o = out + zo + oA;
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[fld[f]]);
+                        Io<S>::st_phi(o + 4 * fs, val[4].x, P.scale[F_PHI]);
+                    }
+                    if (storeB) {
+                        S* o = out + zo + oB;
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[fld[f]]);
+                        Io<S>::st_phi(o + 4 * fs, val[4].y, P.scale[F_PHI]);
+                    }
+                }
+                if (storeA) {
                     sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
                     sum_phi += Io<S>::round_trip_phi(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
                 if (storeB) {
-                    S* o = out + zo + oB;
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[fld[f]]);
-                    Io<S>::st_phi(o + 4 * fs, val[4].y, P.scale[F_PHI]);
                     sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
                     sum_phi += Io<S>::round_trip_phi(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
@@ -456,6 +492,12 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
             n_vzp = phi + b1z;
             n_vzm = phi - b1z;
         }
+        if constexpr (ST) {
+            fence_proxy_async();  // the staging box is read by a TMA store after the barrier
+            // the store issued this iteration has read its box before that box
+            // takes the next iteration's plane
+            if (tid == 0) bulk_wait_read<0>();
+        }
         __syncthreads();
         commit(i + 3);
 #pragma unroll
@@ -471,6 +513,13 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
         s_dyB = n_dyB;
     }
     cp_async_wait<0>();
+    if (ST && tid == 0) {  // the last plane waits in its staging box
+        if (z1 - 1 >= z0) {
+            tma_store_4d(&maps->out, outb + ((z1 - 1 + 8) & 1) * L::OUT_BOX, x0, y0, z1 - 1, 0);
+            bulk_commit();
+        }
+        bulk_wait<0>();
+    }
 
     double a = sum_rho, b = sum_phi;
 #pragma unroll
@@ -496,43 +545,55 @@ __device__ __forceinline__ void step_tile_ce(const StepParams& P, const S* __res
     }
 }
 
-template <int NW, typename S>
+template <int NW, typename S, bool ST>
 __global__ void __launch_bounds__(32 * NW, 1)
-    step_ce_kernel(const __grid_constant__ StepParams P, const S* __restrict__ in, S* __restrict__ out,
-                   const long long* __restrict__ t_in, long long* __restrict__ t_out,
+    step_ce_kernel(const __grid_constant__ StepParams P, const __grid_constant__ TileMaps M, const S* __restrict__ in,
+                   S* __restrict__ out, const long long* __restrict__ t_in, long long* __restrict__ t_out,
                    double* __restrict__ partials) {
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const long long t = *t_in;
-    step_tile_ce<NW, S>(P, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+    step_tile_ce<NW, S, ST>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
     if (blk == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_out = t + 1;
 }
 
-template <int NW, typename S>
-cudaError_t launch_ce_nw(const StepParams& p, const void* in, void* out, const long long* t_in, long long* t_out,
-                         double* partials, cudaStream_t s) {
+template <int NW, typename S, bool ST>
+cudaError_t launch_ce_nw(const StepParams& p, const TileMaps& m, const void* in, void* out, const long long* t_in,
+                         long long* t_out, double* partials, cudaStream_t s) {
     const LaunchShape sh = step_shape(p, ST_FP32);
-    step_ce_kernel<NW, S><<<sh.grid, sh.block, StepCeSmem<NW>::BYTES, s>>>(
-        p, static_cast<const S*>(in), static_cast<S*>(out), t_in, t_out, partials);
+    step_ce_kernel<NW, S, ST><<<sh.grid, sh.block, ST ? StepCeSmem<NW>::BYTES_ST : StepCeSmem<NW>::BYTES, s>>>(
+        p, m, static_cast<const S*>(in), static_cast<S*>(out), t_in, t_out, partials);
     return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_ce_t(const StepParams& p, const void* in, void* out, const long long* t_in, long long* t_out,
-                        double* partials, cudaStream_t s) {
+cudaError_t launch_ce_t(const StepParams& p, const TileMaps* maps, const void* in, void* out, const long long* t_in,
+                        long long* t_out, double* partials, cudaStream_t s) {
+    TileMaps none;
+    memset(&none, 0, sizeof(none));
+    const TileMaps& m = maps ? *maps : none;
+    // staged TMA stores: FP32, an output map made for this block size, not asked off
+    const bool st = sizeof(S) == 4 && m.store && m.block_warps == p.block_warps && !p.plain_stores;
     switch (p.block_warps) {
-        case 8: return launch_ce_nw<8, S>(p, in, out, t_in, t_out, partials, s);
-        case 12: return launch_ce_nw<12, S>(p, in, out, t_in, t_out, partials, s);
+        case 8: return st ? launch_ce_nw<8, S, true>(p, m, in, out, t_in, t_out, partials, s)
+                          : launch_ce_nw<8, S, false>(p, m, in, out, t_in, t_out, partials, s);
+        case 12: return st ? launch_ce_nw<12, S, true>(p, m, in, out, t_in, t_out, partials, s)
+                           : launch_ce_nw<12, S, false>(p, m, in, out, t_in, t_out, partials, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
+template <int NW, typename S, bool ST>
+cudaError_t prepare_ce_nw() {
+    return cudaFuncSetAttribute(step_ce_kernel<NW, S, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(ST ? StepCeSmem<NW>::BYTES_ST : StepCeSmem<NW>::BYTES));
+}
+
 template <typename S>
 cudaError_t prepare_ce_t() {
-    cudaError_t e = cudaFuncSetAttribute(step_ce_kernel<8, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)StepCeSmem<8>::BYTES);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step_ce_kernel<12, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)StepCeSmem<12>::BYTES);
+    cudaError_t e = prepare_ce_nw<8, S, false>();
+    if (e == cudaSuccess) e = prepare_ce_nw<12, S, false>();
+    if (e == cudaSuccess) e = prepare_ce_nw<8, S, true>();
+    if (e == cudaSuccess) e = prepare_ce_nw<12, S, true>();
     return e;
 }
 
@@ -548,11 +609,11 @@ cudaError_t prepare_kernels_ce(int storage) {
 }
 
 cudaError_t launch_step_ce(const StepParams& p, int storage, const void* in, void* out, const long long* t_in,
-                           long long* t_out, double* partials, cudaStream_t s) {
+                           long long* t_out, double* partials, cudaStream_t s, const TileMaps* maps) {
     switch (storage) {
-        case ST_FP32: return launch_ce_t<float>(p, in, out, t_in, t_out, partials, s);
-        case ST_FP16: return launch_ce_t<__half>(p, in, out, t_in, t_out, partials, s);
-        case ST_BF16: return launch_ce_t<__nv_bfloat16>(p, in, out, t_in, t_out, partials, s);
+        case ST_FP32: return launch_ce_t<float>(p, maps, in, out, t_in, t_out, partials, s);
+        case ST_FP16: return launch_ce_t<__half>(p, maps, in, out, t_in, t_out, partials, s);
+        case ST_BF16: return launch_ce_t<__nv_bfloat16>(p, maps, in, out, t_in, t_out, partials, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -236,3 +236,16 @@ def test_departs_from_projection_closure_as_the_oracle_does():
     d_gpu = g_ce[1] - g_pr[1]
     d_orc = r_ce.moments()[1] - r_pr.moments()[1]
     assert np.max(np.abs(d_gpu - d_orc)) < 1e-3 * np.max(np.abs(d_orc)) + 1e-7
+
+
+@pytest.mark.parametrize("block_warps", [8, 12])
+def test_staged_stores_equal_plain_stores(block_warps):
+    """FP32 grids with 16-byte rows write finished planes through a staging box
+    and one TMA store per plane; the plain-store form writes the same bits."""
+    for w in (inputs.jet_workload(64, 50, 40, diameter=10, noise=0.01, seed=5),
+              inputs.droplet_workload(48, radius=12.0)):
+        a, sa, _ = gpu_run(w, 12, block_warps=block_warps)
+        b, sb, _ = gpu_run(w, 12, block_warps=block_warps, plain_stores=True)
+        for k in (0, 1, 3):
+            assert np.array_equal(a[k], b[k])
+        assert sa == sb
