@@ -245,6 +245,15 @@ __device__ __forceinline__ void tmem_wait_ld(float (&v)[40]) {
                  :
                  : "memory");
 }
+// The same for 48 values.
+__device__ __forceinline__ void tmem_wait_ld48(float (&v)[48]) {
+    tmem_wait_ld(reinterpret_cast<float(&)[40]>(v));
+    asm volatile(""
+                 : "+f"(v[40]), "+f"(v[41]), "+f"(v[42]), "+f"(v[43]), "+f"(v[44]), "+f"(v[45]), "+f"(v[46]),
+                   "+f"(v[47])
+                 :
+                 : "memory");
+}
 // Waits for this thread's TMEM stores (their source registers may then be reused).
 __device__ __forceinline__ void tmem_wait_st(const float (&v)[40]) {
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::"f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]),
@@ -254,6 +263,12 @@ __device__ __forceinline__ void tmem_wait_st(const float (&v)[40]) {
     asm volatile("" ::"f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]),
                  "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31]), "f"(v[32]), "f"(v[33]), "f"(v[34]),
                  "f"(v[35]), "f"(v[36]), "f"(v[37]), "f"(v[38]), "f"(v[39])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st48(const float (&v)[48]) {
+    tmem_wait_st(reinterpret_cast<const float(&)[40]>(v));
+    asm volatile("" ::"f"(v[40]), "f"(v[41]), "f"(v[42]), "f"(v[43]), "f"(v[44]), "f"(v[45]), "f"(v[46]),
+                 "f"(v[47])
                  : "memory");
 }
 
@@ -490,29 +505,8 @@ __device__ __forceinline__ void interface_nb(const float (&zS)[4], const float (
 // (footprint column lane + 1), lane 31 the column left of lane 0's.
 __device__ __forceinline__ int own_column(int lane) { return lane == 31 ? 0 : lane + 1; }
 
-// Interface terms of the staged row pair (tile rows 2w and 2w+1; .x / .y),
-// from z combinations stored per phase-field element as float4 {S, D, L, phi}
-// with S = 4 phi + (phi(z+1) + phi(z-1)), D = phi(z+1) - phi(z-1),
-// L = (phi(z+1) + phi(z-1)) - 2 phi: one 16-byte load per element.
-template <int NPH>
-__device__ __forceinline__ void interface4(const float4* zb, int lane, int w, float sig_half, float eps2,
-                                           float2& phi, float2& Fx, float2& Fy, float2& Fz, float2& nxv,
-                                           float2& nyv, float2& nzv) {
-    float zS[4], zD[4], zL[4];
-    const int col = own_column(lane);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const float4 v = zb[col + PHX * (2 * w + r)];
-        zS[r] = v.x;
-        zD[r] = v.y;
-        zL[r] = v.z;
-        if (r == 1) phi.x = v.w;
-        if (r == 2) phi.y = v.w;
-    }
-    interface_nb(zS, zD, zL, lane, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv);
-}
-
-// The same from z combinations stored as three planes of the footprint
+// Interface terms of the staged row pair (tile rows 2w and 2w+1; .x / .y)
+// from z combinations stored as three planes of the footprint
 // ([3][NPH]: phi, phi(z+1) + phi(z-1), phi(z+1) - phi(z-1)).
 template <int NPH>
 __device__ __forceinline__ void interface2(const float* zb, int lane, int w, float sig_half, float eps2,

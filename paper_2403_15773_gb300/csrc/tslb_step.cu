@@ -10,15 +10,16 @@
 // Per staged node and plane the kernel
 //   1. reads the moments (rho - 1, u, P) and the phase field of the node and of
 //      its ghost images: one thread loads each plane's boxes with TMA
-//      (cp.async.bulk.tensor, mbarrier completion) a plane or two ahead, and
-//      ghosts of mirror / copy faces read their source inside the box; ghosts
-//      across periodic faces read theirs from small side boxes loaded with
-//      the plane (FP32 kernels of 8 and 12 warps); the remaining tiles whose
-//      ghost sources leave the box load element by element (cp.async, or
-//      16-bit loads through registers);
-//   2. evaluates grad phi and its Hessian with the isotropic D3Q27 stencils,
-//      the normal n, the curvature kappa = div n and the surface-tension force
-//      F = -(sigma/2) kappa grad phi (Sec. 2.2);
+//      (cp.async.bulk.tensor, mbarrier completion) one or two planes ahead,
+//      and ghosts of mirror / copy faces read their source inside the box;
+//      ghosts across periodic faces read theirs from small side boxes loaded
+//      with the plane (FP32 kernels of 8 and 12 warps); the remaining tiles
+//      whose ghost sources leave the box load element by element (cp.async,
+//      or 16-bit loads through registers);
+//   2. evaluates grad phi and its Hessian with the isotropic D3Q27 stencils
+//      (the phase field of three planes read straight from the ring of
+//      loaded planes), the normal n, the curvature kappa = div n and the
+//      surface-tension force F = -(sigma/2) kappa grad phi (Sec. 2.2);
 //   3. forms the post-collision populations of the node in Hermite form,
 //        f_i^post = w_i [A0 + c.A1/cs2 + H2:A2/(2 cs^4) + H3:A3/(6 cs^6)],
 //      with A1 = j + F, A2 = rho u u + (1-omega) Pi^neq + (1-omega/2)(uF + Fu),
@@ -40,6 +41,10 @@
 //      or with plain stores in the kernel form without the box; 16-bit: plain
 //      stores), and accumulates the FP64 block partials of sum(rho - 1),
 //      sum(phi).
+// Steps 1-3 and the x and y populations of a plane (phase (d)) and the y and
+// z shifts and the output of the plane before it (phase (e)) run in one
+// stretch of code per plane with one block barrier: a software pipeline whose
+// y exchange is double-buffered by plane parity.
 //
 // All arithmetic is FP32 and works with deviations from the rest state
 // (rho - 1, Pi - cs2 I) so that no O(1) terms cancel.
@@ -74,7 +79,6 @@ struct Step2Smem {
     // (finished planes leave by TMA store; 16-bit storage uses plain stores)
     static constexpr bool kFp32 = sizeof(S) == 4;
     static constexpr int TXS = TX;
-    static constexpr bool kTmaStore = kFp32 && ST;
     // blocks of more than 12 warps keep the carries of the z march in tensor
     // memory between planes (registers: 65536 / threads)
     static constexpr bool TC = NW > 12;
@@ -99,40 +103,32 @@ struct Step2Smem {
     static constexpr size_t MOM_SLOT = WR ? MC + r128(MC_BYTES) : r128(MOM_BOX);
     static constexpr size_t PHI_SLOT = WR ? PC + r128(PC_BYTES) : r128(PHI_BOX);
     // planes between the load of a plane's moments and their use (the phase
-    // field is loaded two planes further ahead); 16 warps: shared memory
-    // holds one plane less
+    // field is loaded one plane further ahead)
     static constexpr int PF = NW <= 8 ? 2 : 1;
     static constexpr int MS = PF + 1, PS = PF + 3, NB = PF + 2;      // moment slots, phase slots, mbarriers
     static constexpr size_t MOM = 0;                                 // [MS] moment boxes
     static constexpr size_t RING = MOM + MS * MOM_SLOT;              // [PS] phase-field boxes
     static constexpr int EPT = (NPH + NT - 1) / NT;                  // phase-field elements per thread
-    static constexpr size_t ZC = RING + PS * PHI_SLOT;               // [ZCN][EPT * NT] float4 z combinations
-    static constexpr size_t ZC_BUF = 16 * (size_t)EPT * NT;
-    static constexpr size_t OUT_BOX = kTmaStore ? sizeof(float) * NFIELDS * TY * TXS : 0;  // [11][TY][TXS]
+    static constexpr size_t YX_BUF = sizeof(float) * 20 * (size_t)NT;  // one y exchange [20][NT]
+    static constexpr size_t YX = RING + PS * PHI_SLOT;               // [2][20][NT] y exchange (plane parity)
+    static constexpr size_t OUT_BOX = sizeof(float) * NFIELDS * TY * TXS;  // [11][TY][TXS]
     static constexpr size_t OUT_SLOT = r128(OUT_BOX);
-    // bytes for zcn z-combination buffers and outn output staging boxes
-    static constexpr size_t bytes_for(int zcn, int outn) {
-        return r128(ZC + zcn * ZC_BUF + sizeof(float) * 20 * NT) + outn * OUT_SLOT + NB * sizeof(uint64_t) + 16 +
-               128;  // mbarriers, the TMEM address, alignment slack of the base
-    }
+    static constexpr size_t OUT = r128(YX + 2 * YX_BUF);             // [2] output staging boxes
+    static constexpr size_t TAIL = NB * sizeof(uint64_t) + 16 + 128;  // mbarriers, TMEM address, base slack
     static constexpr size_t kMax = 227 * 1024;
-    // Two z-combination buffers let the next plane's combinations be formed
-    // amid the collision of this one, two staging boxes let a plane's TMA
-    // store overlap the next plane; where shared memory is short, one of each
-    // (the combinations are then formed after the plane's last reads of them,
-    // the store has the collision phase to finish reading its box).
-    static constexpr int ZCN = bytes_for(2, 2) <= kMax || bytes_for(2, 1) <= kMax ? 2 : 1;
-    static constexpr int OUTN = bytes_for(ZCN, 2) <= kMax ? 2 : 1;
-    static constexpr size_t YX = ZC + ZCN * ZC_BUF;                   // [20][NT] float y exchange
-    static constexpr size_t OUT = r128(YX + sizeof(float) * 20 * NT);  // [OUTN] output staging boxes
+    // Finished planes leave through two staging boxes by TMA store (one plane's
+    // store overlaps the next plane) where shared memory has room for them
+    // (FP32, up to 12 warps); otherwise by plain stores.
+    static constexpr bool kTmaStore = kFp32 && ST && OUT + 2 * OUT_SLOT + TAIL <= kMax;
+    static constexpr int OUTN = kTmaStore ? 2 : 0;
     static constexpr size_t BAR = OUT + OUTN * OUT_SLOT;              // NB mbarriers
     static constexpr size_t TMA_ADDR = BAR + NB * sizeof(uint64_t);   // TMEM column address (TC)
     static constexpr size_t BYTES = TMA_ADDR + 16 + 128;              // + alignment slack of the base
-    // TMEM: 64 columns per warp for the 40 carries, four warps per lane quarter
-    static constexpr uint32_t TM_COLS = 256;
+    // TMEM: 128 columns per warp (four warps per lane quarter): the 40 carries
+    // of the z march at columns 0 .. 39, the 48 values (d) hands to (e) at 64 .. 111
+    static constexpr uint32_t TM_COLS = 512;
     static_assert(MAXOFFM + 32 <= MW && MAXOFFP + PHX <= PW, "box too narrow for the aligned tile");
     static_assert(!kTmaStore || (TXS * sizeof(S)) % 16 == 0, "store box rows must be 16-byte multiples");
-    static_assert(BYTES == bytes_for(ZCN, OUTN), "layout");
     static_assert(BYTES <= kMax, "more shared memory than a block can have");
     static_assert(!TC || NW <= 16, "TMEM: at most four warps share a lane quarter");
 };
@@ -168,15 +164,13 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     auto mslot = [](int q) { return (q + 12) % MS; };
     auto pslot = [](int q) { return (q + 20) % PS; };
     auto bslot = [](int i) { return (i + 12) % (PF + 1); };
-    // z-combination buffer of plane q, output staging box of plane q
-    auto zbuf = [](int q) { return L::ZCN == 2 ? ((q + 8) & 1) : 0; };
-    auto obuf = [](int q) { return L::OUTN == 2 ? ((q + 8) & 1) : 0; };
+    // output staging box and y-exchange buffer of plane q
+    auto obuf = [](int q) { return (q + 8) & 1; };
     constexpr int BPRO = PF + 1;  // mbarrier of the prologue loads
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* const sm = align128(smem_raw);
     S* const momb = reinterpret_cast<S*>(sm + L::MOM);
     S* const ring = reinterpret_cast<S*>(sm + L::RING);
-    float4* const zc = reinterpret_cast<float4*>(sm + L::ZC);
     float* const yx = reinterpret_cast<float*>(sm + L::YX);
     float* const outb = reinterpret_cast<float*>(sm + L::OUT);
     uint64_t* const bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
@@ -270,47 +264,66 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         mrdA = rA;
         mrdB = rB;
     }
-    int pxy[EPT], prd[EPT], pres[EPT];
-    float phib[EPT];
+    // Where the phase field of footprint node (row r, column c) is read in a
+    // ring slot: its own box position (element-wise loads fetch the
+    // ghost-resolved source into it) or, for TMA tiles, the box position of
+    // its resolved source (WR: the side boxes); nodes beyond the ghost layers
+    // the stencils reach keep their own position.  ok: the source lies in the
+    // boxes a TMA tile loads.
     const bool inlet_face = P.face[4] == BC_INLET;
     const bool inlet_planes = inlet_face && z0 < 2;
+    auto phi_source = [&](int r, int c, int& own, int& res, int& src_xy, float& phib_v, bool& ok) {
+        float sg;
+        const int psx = resolve_axis(x0 - 2 + c, nx, P.face[0], P.face[1], sg, unused);
+        const int psy = resolve_axis(y0 - 2 + r, ny, P.face[2], P.face[3], sg, unused);
+        const int gxe = x0 - 2 + c, gye = y0 - 2 + r;
+        const bool used = gxe >= -2 && gxe <= nx + 1 && gye >= -2 && gye <= ny + 1;
+        src_xy = psx + nx * psy;
+        own = r * PW + c + offp;
+        res = used ? (psy - yp) * PW + (psx - xp) : own;
+        const bool wxe = WR && perx && (gxe < 0 || gxe >= nx), wye = WR && pery && (gye < 0 || gye >= ny);
+        if (used && (wxe || wye)) {  // WR: phase-field side boxes
+            const int px0 = (int)(L::PX / sizeof(S)), py0 = (int)(L::PY / sizeof(S)), pc0 = (int)(L::PC / sizeof(S));
+            if (!wye) {
+                res = px0 + (psy - yp) * 4 + (psx - xs0);
+                ok = ok && psy >= yp && psy - yp < NR + 2 && psx >= xs0 && psx - xs0 < 4;
+            } else if (!wxe) {
+                res = py0 + (psy - ysp) * PW + (psx - xp);
+                ok = ok && psy >= ysp && psy - ysp < 2 && psx >= xp && psx - xp < PW;
+            } else {
+                res = pc0 + (psy - ysp) * 4 + (psx - xs0);
+                ok = ok && psy >= ysp && psy - ysp < 2 && psx >= xs0 && psx - xs0 < 4;
+            }
+        } else {
+            ok = ok && (!used || (psx >= xp && psx - xp < PW && psy >= yp && psy - yp < NR + 2));
+        }
+        phib_v = inlet_planes ? inlet_phi(P, psx, psy) : 0.f;
+    };
+    // the footprint nodes this thread loads element by element (idx = tid + e NT)
+    int pxy[EPT], prd[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
         const int idx = tid + e * NT;
         pxy[e] = 0;
-        prd[e] = pres[e] = 0;
-        phib[e] = 0.f;
+        prd[e] = 0;
         if (idx < NPH) {
-            float sg;
-            const int r = idx / PHX, c = idx % PHX;
-            const int psx = resolve_axis(x0 - 2 + c, nx, P.face[0], P.face[1], sg, unused);
-            const int psy = resolve_axis(y0 - 2 + r, ny, P.face[2], P.face[3], sg, unused);
-            const int gxe = x0 - 2 + c, gye = y0 - 2 + r;
-            const bool used = gxe >= -2 && gxe <= nx + 1 && gye >= -2 && gye <= ny + 1;
-            pxy[e] = psx + nx * psy;
-            prd[e] = r * PW + c + offp;
-            pres[e] = used ? (psy - yp) * PW + (psx - xp) : prd[e];
-            const bool wxe = WR && perx && (gxe < 0 || gxe >= nx), wye = WR && pery && (gye < 0 || gye >= ny);
-            if (used && (wxe || wye)) {  // WR: phase-field side boxes
-                const int px0 = (int)(L::PX / sizeof(S)), py0 = (int)(L::PY / sizeof(S)), pc0 = (int)(L::PC / sizeof(S));
-                if (!wye) {
-                    pres[e] = px0 + (psy - yp) * 4 + (psx - xs0);
-                    inbox = inbox && psy >= yp && psy - yp < NR + 2 && psx >= xs0 && psx - xs0 < 4;
-                } else if (!wxe) {
-                    pres[e] = py0 + (psy - ysp) * PW + (psx - xp);
-                    inbox = inbox && psy >= ysp && psy - ysp < 2 && psx >= xp && psx - xp < PW;
-                } else {
-                    pres[e] = pc0 + (psy - ysp) * 4 + (psx - xs0);
-                    inbox = inbox && psy >= ysp && psy - ysp < 2 && psx >= xs0 && psx - xs0 < 4;
-                }
-            } else {
-                inbox = inbox && (!used || (psx >= xp && psx - xp < PW && psy >= yp && psy - yp < NR + 2));
-            }
-            if (inlet_planes) phib[e] = inlet_phi(P, psx, psy);
+            int res;
+            float pb;
+            phi_source(idx / PHX, idx % PHX, prd[e], res, pxy[e], pb, inbox);
         }
     }
-    // TMEM for the z-march carries (blocks of more than 12 warps): warp 0
-    // allocates the block's columns; each warp uses 64 columns of its lane quarter
+    // the footprint nodes the interface stencil of this thread's row pair
+    // reads: rows 2w .. 2w + 3 of its own column (lane 31: column 0)
+    int rd4[4], res4[4];
+    float phib4[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int sxy;
+        phi_source(2 * w + r, own_column(lane), rd4[r], res4[r], sxy, phib4[r], inbox);
+    }
+    // TMEM for the z-march carries and the handoffs (blocks of more than 12
+    // warps): warp 0 allocates the block's columns; each warp uses 128 columns
+    // of its lane quarter
     [[maybe_unused]] uint32_t tm_base = 0, tm_addr = 0;
     [[maybe_unused]] uint32_t* const tm_slot = reinterpret_cast<uint32_t*>(sm + L::TMA_ADDR);
     if constexpr (L::TC) {
@@ -321,7 +334,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     if constexpr (L::TC) {
         tmem_fence_after();
         tm_base = *tm_slot;
-        tm_addr = tm_base + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(w >> 2) * 64u;
+        tm_addr = tm_base + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(w >> 2) * 128u;
     }
     if (tma) {
         if constexpr (!WR) {  // (WR: mrdA / mrdB set above)
@@ -329,7 +342,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             mrdB = resB;
         }
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) prd[e] = pres[e];
+        for (int r = 0; r < 4; ++r) rd4[r] = res4[r];
     } else if constexpr (WR) {  // element-wise after all: own positions, box stride
         mrdA = (2 * w) * MW + lane + offm;
         mrdB = mrdA + MW;
@@ -456,29 +469,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         phase ^= 1u << kb;
         pend &= ~(1u << kb);
     };
-    // z combinations {S, D, L, phi} of the phase field at plane q from the
-    // ring planes q - 1, q, q + 1 (see interface4) into the z-combination
-    // buffer of q's parity; inlet planes are imposed.  Each thread combines
-    // the phase-field elements it loads itself (element-wise loads need no
-    // barrier before it).
-    auto zcombine = [&](int q) {
-        const S* pm = ring + pslot(q - 1) * PSL;
-        const S* pc = ring + pslot(q) * PSL;
-        const S* pp = ring + pslot(q + 1) * PSL;
-        const bool im = inlet_face && q - 1 < 0, ic = inlet_face && q < 0;
-        const float inv = P.inv_scale[F_PHI];
-        // (elements beyond NPH read box position 0 and fill padding of zc)
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-            const float a = im ? phib[e] : Io<S>::cvt_phi(pm[prd[e]], inv);
-            const float b = ic ? phib[e] : Io<S>::cvt_phi(pc[prd[e]], inv);
-            const float c = Io<S>::cvt_phi(pp[prd[e]], inv);
-            const float s = c + a;
-            zc[zbuf(q) * (EPT * NT) + tid + e * NT] = make_float4(fmaf(4.f, b, s), c - a, fmaf(-2.f, b, s), b);
-        }
-    };
-
-    // prologue: phase field at planes z0-2 .. z0+PF, moments at planes z0-1 .. z0+PF-2
+    // prologue: phase field at planes z0-2 .. z0+PF-1, moments at planes z0-1 .. z0+PF-2
     float sgz_cur = 1.f;
     int inl_cur = 0;
     if (tma) {
@@ -486,12 +477,12 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             float sg;
             int in2 = 0;
             unsigned bytes = PF * mbytes;
-            for (int q = z0 - 2; q <= z0 + PF; ++q)
+            for (int q = z0 - 2; q <= z0 + PF - 1; ++q)
                 if (!(inlet_face && q < 0)) bytes += pbytes;
             fence_proxy_async();
             // (P.test_stall == 1: 16 bytes more than the copies deliver, so the wait below expires)
             mbar_expect_tx(bar + BPRO, bytes + (P.test_stall == 1 ? 16u : 0u));
-            for (int q = z0 - 2; q <= z0 + PF; ++q)
+            for (int q = z0 - 2; q <= z0 + PF - 1; ++q)
                 if (!(inlet_face && q < 0)) {
                     const int z = resolve_axis(q, nz, P.face[4], P.face[5], sg, in2);
                     tma_load_3d(ring + pslot(q) * PSL, &maps->phi, xp, yp, z, bar + BPRO);
@@ -505,7 +496,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         }
         pend |= 1u << BPRO;
     } else {
-        for (int q = z0 - 2; q <= z0 + PF; ++q) {
+        for (int q = z0 - 2; q <= z0 + PF - 1; ++q) {
             issue(true, q, false, 0, BPRO);
             commit(true, q, false, 0);
         }
@@ -518,8 +509,6 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     cp_async_commit();
     cp_async_wait<0>();
     wait_bar(BPRO);
-    __syncthreads();
-    zcombine(z0 - 1);
 
     // z march carries: for the groups whose z moments 1, 2 are needed
     // (g < 3) p(i-2), z(i-1) and p(i-1); for the others (and phi) the partial
@@ -570,46 +559,184 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     const float om1 = 1.f - P.omega, fo = 1.f - 0.5f * P.omega;
     const float sig_half = -0.5f * P.sigma;
 
-    // March over planes i = z0 - 1 .. z1 with two barriers per plane:
-    //   B: the y exchange of the previous plane has been read, the ring and
-    //      moment slots loaded next and the z-combination buffer written
-    //      next are free;
-    //   loads of phi(i + 2 + PF) and the moments of i + PF; wait for those of
-    //      phi(i + 2) and the moments of i (issued PF planes earlier);
-    //   (d) stencils of plane i, z combinations of plane i + 1 (ring planes
-    //      i .. i + 2, into the other z-combination buffer; 16-warp blocks at
-    //      the end of (e)), collision, x sweep and y populations of plane i;
-    //   A: the y exchange of plane i and the z combinations of i + 1 are
-    //      complete;
-    //   (e) y shift and moments, z shift and moments of plane i, output of
-    //      plane i - 1.
-    // The values (d) hands to (e) live in registers only across barrier A.
-    for (int i = z0 - 1; i <= z1; ++i) {
+    // Software-pipelined march, one barrier per iteration i = z0 - 1 .. z1 + 1:
+    //   barrier: the y exchange and handoffs of plane i - 1 are complete; the
+    //      y exchange of plane i - 2 has been read, so plane i reuses its
+    //      buffer; the ring and moment slots loaded next are free;
+    //   store of plane i - 3 (staged two iterations ago);
+    //   loads of phi(i + 1 + PF) and the moments of i + PF; wait for those of
+    //      phi(i + 1) and the moments of i (issued PF iterations earlier);
+    //   (e) plane i - 1: y shift and moments, z shift and moments, output of
+    //      plane i - 2 (into its staging box);
+    //   (d) plane i: interface stencils (phase field of planes i - 1 .. i + 1),
+    //      collision, x sweep, y populations into the y exchange of plane i.
+    // (e) of one plane and (d) of the next share one stretch of code without a
+    // barrier between them; the values (d) hands to (e) live in registers
+    // across one barrier.
+    float2 hYZ[9];
+    float hPA[9], hMB[9];
+    float2 h_hx = bc(0.f), h_vzp = bc(0.f), h_vzm = bc(0.f);
+    float h_dyA = 0.f, h_dyB = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        hYZ[k] = bc(0.f);
+        hPA[k] = hMB[k] = 0.f;
+    }
+    for (int i = z0 - 1; i <= z1 + 1; ++i) {
         if (__syncthreads_or(dead)) break;
-        // z mirror sign and inlet flag of plane i (its moments were loaded by
-        // the prologue or PF iterations ago)
-        inl_cur = 0;
-        resolve_axis(i, nz, P.face[4], P.face[5], sgz_cur, inl_cur);
-        // plane i - 2 was staged by the previous iteration (and fenced): store it
-        if (tst && tid == 0 && i >= z0 + 2) {
-            tma_store_4d(&maps->out, outb + obuf(i - 2) * OSL, x0, y0, i - 2, 0);
+        const bool dd = i <= z1;  // (d) of plane i in this iteration
+        // plane i - 3 was staged two iterations ago (and fenced): store it
+        if (tst && tid == 0 && i >= z0 + 3) {
+            tma_store_4d(&maps->out, outb + obuf(i - 3) * OSL, x0, y0, i - 3, 0);
             bulk_commit();
         }
-        const bool do_m = i + PF <= z1, do_p = i + 2 + PF <= z1 + 1;
-        const int kb = bslot(i);
-        if ((do_m || do_p) && issue(do_p, i + 2 + PF, do_m, i + PF, kb)) pend |= 1u << kb;
-        if (!tma) {
-            cp_async_commit();
-            cp_async_wait<PF>();
+        const bool do_m = dd && i + PF <= z1, do_p = dd && i + 1 + PF <= z1 + 1;
+        if (dd) {
+            // z mirror sign and inlet flag of plane i (its moments were loaded by
+            // the prologue or PF iterations ago)
+            inl_cur = 0;
+            resolve_axis(i, nz, P.face[4], P.face[5], sgz_cur, inl_cur);
+            const int kb = bslot(i);
+            if ((do_m || do_p) && issue(do_p, i + 1 + PF, do_m, i + PF, kb)) pend |= 1u << kb;
+            if (!tma) cp_async_commit();
+            wait_bar(bslot(i + 1));  // == bslot(i - PF)
         }
-        wait_bar(bslot(i + 1));  // == bslot(i - PF)
 
-        float2 hYZ[9];
-        float hPA[9], hMB[9];
-        float2 h_hx, h_vzp, h_vzm;
-        float h_dyA, h_dyB;
-        // (d) plane i: stencils, collision, x sweep, y populations -> yx and registers
-        {
+        // (e) plane i - 1: y shift and moments, z shift and moments, output of plane i - 2
+        if (i >= z0) {
+            if constexpr (L::TC) {  // the handoffs of (d) of plane i - 1, parked in TMEM
+                float c[48];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) tmem_ld8(tm_addr + 64u + 8u * k, c + 8 * k);
+                tmem_wait_ld48(c);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    hYZ[k] = make_float2(c[2 * k], c[2 * k + 1]);
+                    hPA[k] = c[18 + k];
+                    hMB[k] = c[27 + k];
+                }
+                h_hx = make_float2(c[36], c[37]);
+                h_vzp = make_float2(c[38], c[39]);
+                h_vzm = make_float2(c[40], c[41]);
+                h_dyA = c[42];
+                h_dyB = c[43];
+            }
+            const float* yb = yx + obuf(i - 1) * (20 * NT);
+            const float* yprev = yb + (w > 0 ? tid - 32 : tid);       // row 2w-1
+            const float* ynext = yb + (w < NW - 1 ? tid + 32 : tid);  // row 2w+2
+            float2 Y[3][3][3];
+#pragma unroll
+            for (int qx = 0; qx < 3; ++qx)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int k = 3 * qx + c;
+                    const float2 qp = make_float2(yprev[(2 * k) * NT], hPA[k]);
+                    const float2 qm = make_float2(hMB[k], ynext[(2 * k + 1) * NT]);
+                    const float2 s = qp + qm;
+                    Y[qx][0][c] = s + hYZ[k];
+                    Y[qx][1][c] = qp - qm;
+                    Y[qx][2][c] = s;
+                }
+            const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], h_dyB) + make_float2(h_dyA, ynext[19 * NT]), h_hx);
+
+            if constexpr (L::TC) {
+                float c[40];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) tmem_ld8(tm_addr + 8u * k, c + 8 * k);
+                tmem_wait_ld(c);
+                carries_unpack(c);
+            }
+            const int gqx[6] = {0, 1, 0, 2, 0, 1}, gqy[6] = {0, 0, 1, 0, 2, 1};
+            float2 O0[6], O1[6], O2[6];
+#pragma unroll
+            for (int g = 0; g < 6; ++g) {
+                const Tri2 tr = pops2(Y[gqx[g]][gqy[g]][0], Y[gqx[g]][gqy[g]][1], Y[gqx[g]][gqy[g]][2]);
+                if (g < 3) {
+                    O0[g] = cPP[g] + cZ[g] + tr.m;
+                    O1[g] = cPP[g] - tr.m;
+                    O2[g] = cPP[g] + tr.m;
+                    cPP[g] = cP[g];
+                    cZ[g] = tr.z;
+                } else {
+                    O0[g] = cA[g] + tr.m;
+                    cA[g] = cP[g] + tr.z;
+                }
+                cP[g] = tr.p;
+            }
+            const float2 phin = mad(0.125f, h_vzm, cAph);
+            cAph = mad(0.125f, cVP, hxy);
+            cVP = h_vzp;
+            if constexpr (L::TC) carries_store();
+
+            if (i >= z0 + 2) {  // (every lane computes; halo and out-of-grid lanes do not write)
+                const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
+                const float2 rn = bc(1.f) + dr, irn = rcp2(rn);
+                const float2 ux = jx * irn, uy = jy * irn, uz = jz * irn;
+                const float2 rux = rn * ux, ruy = rn * uy, ruz = rn * uz;
+                const float2 mdr = (-1.f / 3.f) * dr;
+                float2 val[NFIELDS];
+                val[F_DRHO] = dr;
+                val[F_UX] = ux;
+                val[F_UY] = uy;
+                val[F_UZ] = uz;
+                val[F_PXX] = O0[3] + mdr - rux * ux;
+                val[F_PYY] = O0[4] + mdr - ruy * uy;
+                val[F_PZZ] = O2[0] + mdr - ruz * uz;
+                val[F_PXY] = O0[5] - rux * uy;
+                val[F_PXZ] = O1[1] - rux * uz;
+                val[F_PYZ] = O1[2] - ruy * uz;
+                val[F_PHI] = phin;
+                const long long zo = nxy * (i - 2);
+                if (tst) {  // into the staging box of plane i - 2: [field][tile row][tile column]
+                    float* ob = outb + obuf(i - 2) * OSL + (2 * w - 1) * TX + (lane - 1);
+                    if (storeA) {
+#pragma unroll
+                        for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX] = val[f].x;
+                    }
+                    if (storeB) {
+#pragma unroll
+                        for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX + TX] = val[f].y;
+                    }
+                } else {
+                    if (storeA) {
+                        S* o = out + zo + sxyA;
+#pragma unroll
+                        for (int f = 0; f < F_PHI; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
+                        Io<S>::st_phi(o + F_PHI * fs, val[F_PHI].x, P.scale[F_PHI]);
+                    }
+                    if (storeB) {
+                        S* o = out + zo + sxyB;
+#pragma unroll
+                        for (int f = 0; f < F_PHI; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
+                        Io<S>::st_phi(o + F_PHI * fs, val[F_PHI].y, P.scale[F_PHI]);
+                    }
+                }
+                if (storeA) {
+                    sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
+                    sum_phi += Io<S>::round_trip_phi(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                }
+                if (storeB) {
+                    sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
+                    sum_phi += Io<S>::round_trip_phi(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
+                }
+                if (P.avg) {  // time sums of the new phi and u_z (FP64)
+                    if (storeA) {
+                        double* a = P.avg + zo + sxyA;
+                        a[0] += (double)phin.x;
+                        a[fs] += (double)uz.x;
+                    }
+                    if (storeB) {
+                        double* a = P.avg + zo + sxyB;
+                        a[0] += (double)phin.y;
+                        a[fs] += (double)uz.y;
+                    }
+                }
+            }
+        }
+
+        // (d) plane i: stencils, collision, x sweep, y populations -> y exchange of
+        // plane i and the handoffs to its (e) in the next iteration
+        if (dd) {
             const S* mA = momb + mslot(i) * MSL + mrdA;
             const S* mB = momb + mslot(i) * MSL + mrdB;
             auto ld2 = [&](int f) {
@@ -630,19 +757,35 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                 uz = make_float2(ua[2], ub[2]);
             }
 
-            // interface terms from the z combinations of phi at plane i
+            // interface terms from the phase field of planes i - 1, i, i + 1 at
+            // rows 2w .. 2w + 3 of the lane's own column (its z combinations S,
+            // D, L), the neighbour columns by shuffles (interface_nb)
             float2 phi, Fx, Fy, Fz, nxv, nyv, nzv;
-            const float4* zci = zc + zbuf(i) * (EPT * NT);
-            static_assert(TX <= 28, "the interface stencil takes columns from the spare lanes 30, 31");
-            interface4<NPH>(zci, lane, w, sig_half, P.normal_eps2, phi, Fx, Fy, Fz, nxv, nyv, nzv);
+            {
+                static_assert(TX <= 28, "the interface stencil takes columns from the spare lanes 30, 31");
+                const S* pm = ring + pslot(i - 1) * PSL;
+                const S* pc = ring + pslot(i) * PSL;
+                const S* pp = ring + pslot(i + 1) * PSL;
+                const bool im = inlet_face && i - 1 < 0, ic = inlet_face && i < 0;
+                const float inv = P.inv_scale[F_PHI];
+                float zS[4], zD[4], zL[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float a = im ? phib4[r] : Io<S>::cvt_phi(pm[rd4[r]], inv);
+                    const float b = ic ? phib4[r] : Io<S>::cvt_phi(pc[rd4[r]], inv);
+                    const float c = Io<S>::cvt_phi(pp[rd4[r]], inv);
+                    const float s = c + a;
+                    zS[r] = fmaf(4.f, b, s);
+                    zD[r] = c - a;
+                    zL[r] = fmaf(-2.f, b, s);
+                    if (r == 1) phi.x = b;
+                    if (r == 2) phi.y = b;
+                }
+                interface_nb(zS, zD, zL, lane, sig_half, P.normal_eps2, Fx, Fy, Fz, nxv, nyv, nzv);
+            }
             if (inl_cur) {
                 Fx = Fy = Fz = bc(0.f);
                 nxv = nyv = nzv = bc(0.f);
-            }
-            // shared-memory work of the next plane amid the arithmetic of this one
-            // (16-warp blocks, at 128 registers, do it in (e): here it spills)
-            if constexpr (L::ZCN == 2) {
-                if (i < z1) zcombine(i + 1);
             }
 
             // Guo forcing: v = u + F / (2 rho)
@@ -653,7 +796,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
 
             // D3Q7: g_i^post = w_i (B0 + c_i . B1); x terms by shuffles, the
             // y terms of the row pair's edges through shared memory
-            float* yb = yx + tid;
+            float* yb = yx + obuf(i) * (20 * NT) + tid;
             {
                 const float2 ga = P.gamma * (bc(1.f) - phi * phi);
                 const float2 fphi = 4.f * phi;
@@ -704,129 +847,35 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                     hMB[k] = tr.m.y;
                 }
         }
-        // (e) below rewrites the staging box of plane i - 3: its store has read it
-        if (tst && tid == 0) bulk_wait_read<L::OUTN - 1>();
-        __syncthreads();
 
-        // (e) plane i: y shift and moments, z shift and moments, output of plane i - 1
-        {
-            const float* yprev = yx + (w > 0 ? tid - 32 : tid);       // row 2w-1
-            const float* ynext = yx + (w < NW - 1 ? tid + 32 : tid);  // row 2w+2
-            float2 Y[3][3][3];
+        if constexpr (L::TC) {
+            if (dd) {  // park this plane's handoffs in TMEM until its (e) in the next iteration
+                float c[48];
 #pragma unroll
-            for (int qx = 0; qx < 3; ++qx)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int k = 3 * qx + c;
-                    const float2 qp = make_float2(yprev[(2 * k) * NT], hPA[k]);
-                    const float2 qm = make_float2(hMB[k], ynext[(2 * k + 1) * NT]);
-                    const float2 s = qp + qm;
-                    Y[qx][0][c] = s + hYZ[k];
-                    Y[qx][1][c] = qp - qm;
-                    Y[qx][2][c] = s;
+                for (int k = 0; k < 9; ++k) {
+                    c[2 * k] = hYZ[k].x, c[2 * k + 1] = hYZ[k].y;
+                    c[18 + k] = hPA[k];
+                    c[27 + k] = hMB[k];
                 }
-            const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], h_dyB) + make_float2(h_dyA, ynext[19 * NT]), h_hx);
-
-            if constexpr (L::TC) {
-                float c[40];
+                c[36] = h_hx.x, c[37] = h_hx.y, c[38] = h_vzp.x, c[39] = h_vzp.y;
+                c[40] = h_vzm.x, c[41] = h_vzm.y, c[42] = h_dyA, c[43] = h_dyB;
 #pragma unroll
-                for (int k = 0; k < 5; ++k) tmem_ld8(tm_addr + 8u * k, c + 8 * k);
-                tmem_wait_ld(c);
-                carries_unpack(c);
-            }
-            const int gqx[6] = {0, 1, 0, 2, 0, 1}, gqy[6] = {0, 0, 1, 0, 2, 1};
-            float2 O0[6], O1[6], O2[6];
+                for (int k = 44; k < 48; ++k) c[k] = 0.f;
 #pragma unroll
-            for (int g = 0; g < 6; ++g) {
-                const Tri2 tr = pops2(Y[gqx[g]][gqy[g]][0], Y[gqx[g]][gqy[g]][1], Y[gqx[g]][gqy[g]][2]);
-                if (g < 3) {
-                    O0[g] = cPP[g] + cZ[g] + tr.m;
-                    O1[g] = cPP[g] - tr.m;
-                    O2[g] = cPP[g] + tr.m;
-                    cPP[g] = cP[g];
-                    cZ[g] = tr.z;
-                } else {
-                    O0[g] = cA[g] + tr.m;
-                    cA[g] = cP[g] + tr.z;
-                }
-                cP[g] = tr.p;
-            }
-            const float2 phin = mad(0.125f, h_vzm, cAph);
-            cAph = mad(0.125f, cVP, hxy);
-            cVP = h_vzp;
-            if constexpr (L::TC) carries_store();
-
-            if (i >= z0 + 1) {  // (every lane computes; halo and out-of-grid lanes do not write)
-                const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
-                const float2 rn = bc(1.f) + dr, irn = rcp2(rn);
-                const float2 ux = jx * irn, uy = jy * irn, uz = jz * irn;
-                const float2 rux = rn * ux, ruy = rn * uy, ruz = rn * uz;
-                const float2 mdr = (-1.f / 3.f) * dr;
-                float2 val[NFIELDS];
-                val[F_DRHO] = dr;
-                val[F_UX] = ux;
-                val[F_UY] = uy;
-                val[F_UZ] = uz;
-                val[F_PXX] = O0[3] + mdr - rux * ux;
-                val[F_PYY] = O0[4] + mdr - ruy * uy;
-                val[F_PZZ] = O2[0] + mdr - ruz * uz;
-                val[F_PXY] = O0[5] - rux * uy;
-                val[F_PXZ] = O1[1] - rux * uz;
-                val[F_PYZ] = O1[2] - ruy * uz;
-                val[F_PHI] = phin;
-                const long long zo = nxy * (i - 1);
-                if (tst) {  // into the staging box of plane i - 1: [field][tile row][tile column]
-                    float* ob = outb + obuf(i - 1) * OSL + (2 * w - 1) * TX + (lane - 1);
-                    if (storeA) {
-#pragma unroll
-                        for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX] = val[f].x;
-                    }
-                    if (storeB) {
-#pragma unroll
-                        for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX + TX] = val[f].y;
-                    }
-                } else {
-                    if (storeA) {
-                        S* o = out + zo + sxyA;
-#pragma unroll
-                        for (int f = 0; f < F_PHI; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
-                        Io<S>::st_phi(o + F_PHI * fs, val[F_PHI].x, P.scale[F_PHI]);
-                    }
-                    if (storeB) {
-                        S* o = out + zo + sxyB;
-#pragma unroll
-                        for (int f = 0; f < F_PHI; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
-                        Io<S>::st_phi(o + F_PHI * fs, val[F_PHI].y, P.scale[F_PHI]);
-                    }
-                }
-                if (storeA) {
-                    sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                    sum_phi += Io<S>::round_trip_phi(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
-                }
-                if (storeB) {
-                    sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
-                    sum_phi += Io<S>::round_trip_phi(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
-                }
-                if (P.avg) {  // time sums of the new phi and u_z (FP64)
-                    if (storeA) {
-                        double* a = P.avg + zo + sxyA;
-                        a[0] += (double)phin.x;
-                        a[fs] += (double)uz.x;
-                    }
-                    if (storeB) {
-                        double* a = P.avg + zo + sxyB;
-                        a[0] += (double)phin.y;
-                        a[fs] += (double)uz.y;
-                    }
-                }
+                for (int k = 0; k < 6; ++k) tmem_st8(tm_addr + 64u + 8u * k, c + 8 * k);
+                tmem_wait_st48(c);
             }
         }
-
-        if (tst) fence_proxy_async();  // the staging box is read by the TMA store next iteration
-        if constexpr (L::ZCN == 1) {
-            if (i < z1) zcombine(i + 1);
+        // element-wise copies land by the end of the iteration that issued them
+        // (the barrier then publishes them to the threads that read them)
+        if (!tma) cp_async_wait<0>();
+        commit(do_p, i + 1 + PF, do_m, i + PF);
+        if (tst) {
+            fence_proxy_async();  // the staging box is read by a TMA store after the barrier
+            // the store issued this iteration has read its box before the box
+            // takes the plane after next
+            if (tid == 0) bulk_wait_read<0>();
         }
-        commit(do_p, i + 2 + PF, do_m, i + PF);
     }
     // the last plane (z1 - 1) waits in its staging box
     if constexpr (L::TC) tmem_fence_before();
