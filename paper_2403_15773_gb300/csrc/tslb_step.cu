@@ -81,7 +81,7 @@ struct Step2Smem {
     static constexpr int TXS = TX;
     // blocks of more than 12 warps keep the carries of the z march in tensor
     // memory between planes (registers: 65536 / threads)
-    static constexpr bool TC = NW > 12;
+    static constexpr bool TC = NW > 12 || (!kFp32 && NW > 8);
     // box columns: staged columns x0-1 .. x0+30 (moments) and x0-2 .. x0+31
     // (phase field) from the 16-byte boundary below them
     static constexpr int MW = kFp32 ? 36 : 40;
@@ -355,7 +355,10 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     // cp.async straight into shared memory; 16-bit values wait in registers
     // until commit().  Inlet planes of the phase field are never loaded (the
     // imposed values are used directly).  Returns whether bar[kb] got copies.
-    unsigned short rphi[EPT], rmom[2][10];
+    // (16-bit element-wise loads: the raw values wait in registers, the two
+    // rows of a moment field packed into one 32-bit register)
+    unsigned short rphi[EPT];
+    unsigned rmom[10];
     // bytes a plane's phase-field / moment copies deliver (WR: with the side boxes)
     const unsigned pbytes = (unsigned)L::PHI_BOX + (WR ? (wrx ? (unsigned)L::PX_BYTES : 0u) +
                                                              (wry ? (unsigned)L::PY_BYTES : 0u) +
@@ -431,8 +434,8 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                     cp_async4(reinterpret_cast<float*>(mdst + mrdA + f * FS), reinterpret_cast<const float*>(srcA + f * fs));
                     cp_async4(reinterpret_cast<float*>(mdst + mrdB + f * FS), reinterpret_cast<const float*>(srcB + f * fs));
                 } else {
-                    rmom[0][f] = __ldg(reinterpret_cast<const unsigned short*>(srcA + f * fs));
-                    rmom[1][f] = __ldg(reinterpret_cast<const unsigned short*>(srcB + f * fs));
+                    rmom[f] = (unsigned)__ldg(reinterpret_cast<const unsigned short*>(srcA + f * fs)) |
+                              ((unsigned)__ldg(reinterpret_cast<const unsigned short*>(srcB + f * fs)) << 16);
                 }
             }
         }
@@ -452,8 +455,8 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                 unsigned short* dst = reinterpret_cast<unsigned short*>(momb + mslot(qm) * MSL);
 #pragma unroll
                 for (int f = 0; f < 10; ++f) {
-                    dst[mrdA + f * FS] = rmom[0][f];
-                    dst[mrdB + f * FS] = rmom[1][f];
+                    dst[mrdA + f * FS] = (unsigned short)(rmom[f] & 0xffffu);
+                    dst[mrdB + f * FS] = (unsigned short)(rmom[f] >> 16);
                 }
             }
         }
