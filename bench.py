@@ -38,8 +38,9 @@ METRIC = "GLUPS and % of HBM roofline on 1 GB300, FP32 vs FP16-storage vs batche
 UNIT = "GLUPS"
 FIELDS = 11  # stored values per node: rho - 1, u (3), P (6), phi
 # committed ncu summaries of the step kernel per storage type (DRAM bytes per node)
-PROFILE_SUMMARIES = {"fp32": os.path.join(ROOT, "profiles", "step_kernel_jet192_fp32.txt"),
-                     "fp16": os.path.join(ROOT, "profiles", "step_kernel_jet128_fp16.txt")}
+PROFILE_SUMMARIES = {"fp32": os.path.join(ROOT, "profiles", "step_kernel_fp32.txt"),
+                     "fp16": os.path.join(ROOT, "profiles", "step_kernel_fp16.txt")}
+TX = 28  # interior columns of a step-kernel tile
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2403_15773_gb300", "csrc", f)
                   for f in ("tslb_step.cu", "tslb_device.cuh", "tslb_internal.h")]
 
@@ -85,7 +86,7 @@ def profiled_traffic(nodes: int, storage: str = "fp32"):
 
 
 def profiled_fp32_ops(storage: str = "fp32"):
-    """FP32 lane operations per lattice update of the step kernel of `storage`
+    """FP32 lane operations per staged node of the step kernel of `storage`
     from its committed ncu summary (instruction counts), if it was taken on the
     current kernel source."""
     path = PROFILE_SUMMARIES.get(storage)
@@ -94,10 +95,20 @@ def profiled_fp32_ops(storage: str = "fp32"):
     except OSError:
         return None
     sha = re.search(r"kernel_source_sha:\s*(\w+)", txt)
-    ops = re.search(r"fp32_lane_ops_per_update:\s*([0-9.eE+-]+)", txt)
+    ops = re.search(r"fp32_lane_ops_per_staged_node:\s*([0-9.eE+-]+)", txt)
     if not sha or not ops or sha.group(1) != kernel_source_sha():
         return None
     return float(ops.group(1))
+
+
+def staged_per_node(nx: int, ny: int, nz: int, block_warps: int, tile_z: int) -> float:
+    """Nodes the step kernel's tiles stage (32 columns x 2 block_warps rows x
+    (slab + 2) planes each) per interior node of the grid."""
+    ty = 2 * block_warps - 2
+    tz = min(tile_z, nz) if tile_z > 0 else nz
+    bx, by = -(-nx // TX), -(-ny // ty)
+    planes = sum(min(tz, nz - k * tz) + 2 for k in range(-(-nz // tz)))
+    return bx * 32 * by * 2 * block_warps * planes / (nx * ny * nz)
 
 
 class ClockSampler:
@@ -651,15 +662,19 @@ def main():
         "variants": variants,
     }
     if fma is not None:
-        ops = profiled_fp32_ops(args.storage)
+        ops_staged = profiled_fp32_ops(args.storage)
+        sh = res["shape"]
+        ratio = staged_per_node(ws[0].nx, ws[0].ny, ws[0].nz, sh["block_warps"], sh["tile_z"])
+        ops = None if ops_staged is None else ops_staged * ratio
         line["fp32_roofline"] = {
             "bound": "alu", "unit": "FP32 lane-FMA/s", "peak": fma["packed"], "peak_scalar": fma["scalar"],
-            "ops_per_update": ops,
+            "ops_per_update": ops, "staged_per_node": ratio,
             "achieved": None if ops is None else ops * n_grid / per_launch,
             "frac": None if ops is None else ops * n_grid / per_launch / fma["packed"],
             "note": "peak: this run's tslb_fp32_lane_rate (independent FMA chains; packed f32x2 and "
-                    "scalar); ops_per_update: FP32 lane operations (packed x 2) per lattice update "
-                    "counted by ncu on the same kernel source (null when it changed since)"}
+                    "scalar); ops_per_update: FP32 lane operations (packed x 2) per staged node "
+                    "counted by ncu on the same kernel source (null when it changed since) x the "
+                    "nodes the timed tile shape stages per interior node"}
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
