@@ -21,7 +21,10 @@
  *     P = Pi - rho cs2 I - rho u u (the non-equilibrium momentum flux of
  *     Sec. 2 relative to u); phi in [-1, 1], +1 = component A.
  *   - on_device != 0: the pointer is CUDA device memory of the context's
- *     device; 0: host memory (pageable or pinned).
+ *     device; 0: host memory (pageable or pinned).  The moment and phi calls
+ *     (set_state, get_moments, get_phi and their batch forms) read and write
+ *     page-locked host memory directly from their conversion kernels, over
+ *     the host link; pageable host memory goes through a staging copy.
  *   - All work is issued on the context's stream; calls that return data to
  *     the host synchronise that stream.  A context must not be used from two
  *     host threads at once.

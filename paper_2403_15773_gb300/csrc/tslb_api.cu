@@ -345,21 +345,51 @@ Layout layout_for(const std::vector<StepParams>& ps, size_t elem, int storage, b
     return L;
 }
 
+// Device address through which kernels reach host memory at `p` directly
+// (page-locked host memory, mapped into the device's address space), or
+// null for pageable memory (which goes through the staging field).
+const void* mapped_host_alias(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// One caller field into the state.  Device memory and page-locked host memory
+// are read by the conversion kernel itself (the latter over the host link,
+// without a staging copy); pageable host memory is copied to the staging
+// field first.
 tslb_status put_field(tslb_ctx* c, Instance& I, const float* src, int field, int on_device) {
     const float* dsrc = src;
     if (!on_device) {
-        CK(cudaMemcpyAsync(c->staging, src, (size_t)I.N * sizeof(float), cudaMemcpyHostToDevice, c->stream),
-           "host-to-device copy");
-        dsrc = c->staging;
+        dsrc = static_cast<const float*>(mapped_host_alias(src));
+        if (!dsrc) {
+            CK(cudaMemcpyAsync(c->staging, src, (size_t)I.N * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+               "host-to-device copy");
+            dsrc = c->staging;
+        }
     }
     CK(tslb::launch_put_field(I.p, c->storage, dsrc, field, I.buf[c->cur], c->stream), "field conversion");
     return TSLB_OK;
 }
 
+// One state field out to the caller: the conversion kernel writes device
+// memory or page-locked host memory directly, pageable host memory through
+// the staging field.
 tslb_status get_field(tslb_ctx* c, Instance& I, float* dst, int field, int on_device) {
-    float* ddst = on_device ? dst : c->staging;
+    float* ddst = dst;
+    bool staged = false;
+    if (!on_device) {
+        ddst = static_cast<float*>(const_cast<void*>(mapped_host_alias(dst)));
+        if (!ddst) {
+            ddst = c->staging;
+            staged = true;
+        }
+    }
     CK(tslb::launch_get_field(I.p, c->storage, I.buf[c->cur], field, ddst, c->stream), "field conversion");
-    if (!on_device)
+    if (staged)
         CK(cudaMemcpyAsync(dst, c->staging, (size_t)I.N * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
            "device-to-host copy");
     return TSLB_OK;

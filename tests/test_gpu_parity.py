@@ -299,6 +299,29 @@ def test_host_buffer_path_matches_device_path():
     assert np.array_equal(a[3], ph.reshape(s).astype(np.float64))
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_pinned_host_buffers_match_device_path(storage):
+    """Page-locked host buffers are read and written by the conversion
+    kernels directly (no staging copy); the fields are bitwise those of the
+    device-pointer path."""
+    w = inputs.jet_workload(40, 36, 30, diameter=10, noise=0.01, seed=6)
+    rho, u, phi = (torch.from_numpy(a.astype(np.float32).reshape(-1)).pin_memory() for a in w.fields())
+    a, _, _ = gpu_run(w, 10, storage=storage)
+    sim = tslb.Simulation(w, storage=storage)
+    sim.set_state_host(rho, u, phi)
+    sim.step(10)
+    N = w.nodes
+    r, uu, pp, ph = (torch.empty(k * N, dtype=torch.float32).pin_memory() for k in (1, 3, 6, 1))
+    sim.moments_host(r, uu, pp)
+    sim.phi_host(ph)
+    sim.close()
+    s = a[0].shape
+    assert np.array_equal(a[0], r.numpy().reshape(s).astype(np.float64))
+    assert np.array_equal(a[1], uu.numpy().reshape((3,) + s).astype(np.float64))
+    assert np.array_equal(a[2], pp.numpy().reshape((6,) + s).astype(np.float64))
+    assert np.array_equal(a[3], ph.numpy().reshape(s).astype(np.float64))
+
+
 def test_call_order_and_pointer_errors():
     w = inputs.droplet_workload(16)
     sim = tslb.Simulation(w)
