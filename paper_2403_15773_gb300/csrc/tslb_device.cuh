@@ -365,8 +365,20 @@ struct Io<__nv_bfloat16> {
 // together with the packed FP32 instructions of sm_100+ (one instruction, two
 // lanes of arithmetic): .x is the node of row 2w, .y the node of row 2w+1.
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// (packed subtraction: PTX sub.rn.f32x2; an FMA by -1 would hold a constant
+// pair in registers and take the FMA form of the instruction)
 __device__ __forceinline__ float2 operator-(float2 a, float2 b) {
-    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+    float2 d;
+    asm("{\n"
+        " .reg .b64 ra, rb, rd;\n"
+        " mov.b64 ra, {%2, %3};\n"
+        " mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n"
+        "}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
 }
 __device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 operator*(float s, float2 b) { return __fmul2_rn(make_float2(s, s), b); }
@@ -436,10 +448,12 @@ __device__ __forceinline__ float2 l2v(float2 a, float2 b, float2 c) { return mad
 // and the CSF force F = -(sigma/2) kappa grad phi (Sec. 2.2) become
 //   F = (sig_half / 36) (tr Hd - G.H'.G / |G|^2) / |G| * G,
 // where sig_half = -sigma/2 and H' weighs the off-diagonal terms 2 * 36 / 24.
+// keep = 0 gives F = n = 0 (a node that carries no interface terms), keep = 1
+// the terms above.
 __device__ __forceinline__ void interface_x(const float2 (&yS)[3], const float2 (&yDS)[3], const float2 (&yLS)[3],
                                             const float2 (&ySD)[3], const float2 (&yDD)[3], const float2 (&ySL)[3],
                                             float sig_half, float eps2, float2& Fx, float2& Fy, float2& Fz,
-                                            float2& nxv, float2& nyv, float2& nzv) {
+                                            float2& nxv, float2& nyv, float2& nzv, float keep = 1.f) {
     const float2 gx = yS[2] - yS[0];
     const float2 gy = s0v(yDS[0], yDS[1], yDS[2]);
     const float2 gz = s0v(ySD[0], ySD[1], ySD[2]);
@@ -451,7 +465,7 @@ __device__ __forceinline__ void interface_x(const float2 (&yS)[3], const float2 
     const float2 hyz = s0v(yDD[0], yDD[1], yDD[2]);
 
     const float2 m2 = mad(gx, gx, mad(gy, gy, mad(gz, gz, bc(72.f * 72.f * eps2))));
-    const float2 im = make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
+    const float2 im = keep * make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
     nxv = gx * im;
     nyv = gy * im;
     nzv = gz * im;
@@ -484,7 +498,7 @@ __device__ __forceinline__ void ycomb(const float (&zS)[4], const float (&zD)[4]
 // 0 .. 29 (the staged columns of a 28-column tile).
 __device__ __forceinline__ void interface_nb(const float (&zS)[4], const float (&zD)[4], const float (&zL)[4],
                                              int lane, float sig_half, float eps2, float2& Fx, float2& Fy,
-                                             float2& Fz, float2& nxv, float2& nyv, float2& nzv) {
+                                             float2& Fz, float2& nxv, float2& nyv, float2& nzv, float keep = 1.f) {
     float2 yS[3], yDS[3], yLS[3], ySD[3], yDD[3], ySL[3];
     ycomb(zS, zD, zL, yS[1], yDS[1], yLS[1], ySD[1], yDD[1], ySL[1]);
     const int left = (lane + 31) & 31;
@@ -498,7 +512,7 @@ __device__ __forceinline__ void interface_nb(const float (&zS)[4], const float (
     nb(ySD);
     nb(yDD);
     nb(ySL);
-    interface_x(yS, yDS, yLS, ySD, yDD, ySL, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv);
+    interface_x(yS, yDS, yLS, ySD, yDD, ySL, sig_half, eps2, Fx, Fy, Fz, nxv, nyv, nzv, keep);
 }
 
 // Footprint column a lane forms its stencil values for: its own staged column

@@ -148,8 +148,11 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 // gave up on them: its mbarriers and shared memory must then not be reused.
 // maps: tensor maps of `in` for TMA loads, or null (element-wise loads).
 // ST: staged TMA stores (FP32); WR: side boxes for ghosts across periodic
-// faces (FP32, maps with the side-box tensor maps).
-template <int NW, typename S, bool ST, bool WR>
+// faces (FP32, maps with the side-box tensor maps).  TS: this tile's finished
+// planes do leave through the staging boxes (a kernel form with them, and
+// maps with the output map: staged_stores()); a compile-time flag, so that
+// the march has no branch on it.
+template <int NW, typename S, bool ST, bool WR, bool TS>
 __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
                                           S* __restrict__ out, const long long t, const int bx, const int by,
                                           const int bz, double* __restrict__ part) {
@@ -183,7 +186,8 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     const int z1 = min(z0 + P.tile_z, nz);
     const bool use_maps = maps != nullptr && maps->valid && maps->block_warps == NW;
     // finished planes leave through the staging box by TMA store (FP32)
-    const bool tst = L::kTmaStore && use_maps && maps->store;
+    static_assert(!TS || L::kTmaStore, "staged stores need the staging boxes");
+    constexpr bool tst = TS;
     if (use_maps && tid == 0) {
         for (int k = 0; k < NB; ++k) mbar_init(bar + k, 1);
         fence_mbar_init();
@@ -473,8 +477,6 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         pend &= ~(1u << kb);
     };
     // prologue: phase field at planes z0-2 .. z0+PF-1, moments at planes z0-1 .. z0+PF-2
-    float sgz_cur = 1.f;
-    int inl_cur = 0;
     if (tma) {
         if (tid == 0) {
             float sg;
@@ -575,7 +577,12 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     //      collision, x sweep, y populations into the y exchange of plane i.
     // (e) of one plane and (d) of the next share one stretch of code without a
     // barrier between them; the values (d) hands to (e) live in registers
-    // across one barrier.
+    // across one barrier.  (e) and (d) run in every iteration, so that stretch
+    // has no branch: (e) of planes z0 - 2 and z0 - 1 (first two iterations)
+    // and (d) of plane z1 + 1 (last) work on values no stored node depends on
+    // (their own planes are not stored, and the z carries they leave are
+    // overwritten before the first stored plane), and the output stores of an
+    // iteration are predicated on its plane being one of the tile's.
     float2 hYZ[9];
     float hPA[9], hMB[9];
     float2 h_hx = bc(0.f), h_vzp = bc(0.f), h_vzm = bc(0.f);
@@ -585,9 +592,41 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         hYZ[k] = bc(0.f);
         hPA[k] = hMB[k] = 0.f;
     }
+    // The z mirror sign and inlet flag of the planes the march meets: the
+    // ghost plane below the grid (z = -1, tiles with z0 = 0), the one above
+    // (z = nz), interior planes in between.  The imposed inlet velocity of the
+    // inlet ghost plane is drawn once per tile: FP32 writes it over the
+    // velocity of that plane's moment slot (each staged node at the position
+    // it reads, the velocity of its resolved source node, so nodes sharing a
+    // source write the same value), where (d) reads it like any plane;
+    // 16-bit storage keeps it in registers (with the x / y mirror signs) and
+    // selects it for that plane.
+    float sgz_lo = 1.f, sgz_hi = 1.f;
+    int inl_lo = 0, inl_unused = 0;
+    resolve_axis(-1, nz, P.face[4], P.face[5], sgz_lo, inl_lo);
+    resolve_axis(nz, nz, P.face[4], P.face[5], sgz_hi, inl_unused);
+    [[maybe_unused]] float2 iux = bc(0.f), iuy = bc(0.f), iuz = bc(0.f);
+    if (inl_lo && z0 == 0) {
+        float ua[3], ub[3];
+        inlet_velocity(P, sx, syA, t, ua);
+        inlet_velocity(P, sx, syB, t, ub);
+        if constexpr (L::kFp32) {  // (the barrier that starts the march orders these writes before (d) reads them)
+            S* const m = momb + mslot(z0 - 1) * MSL;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                m[mrdA + (1 + f) * (WR ? fsA : FS)] = ua[f];
+                m[mrdB + (1 + f) * (WR ? fsB : FS)] = ub[f];
+            }
+            fence_proxy_async();  // before a later TMA load writes this slot again
+        } else {
+            iux = make_float2(ua[0] * sgx, ub[0] * sgx);
+            iuy = make_float2(ua[1] * sgyA, ub[1] * sgyB);
+            iuz = make_float2(ua[2], ub[2]);
+        }
+    }
     for (int i = z0 - 1; i <= z1 + 1; ++i) {
         if (__syncthreads_or(dead)) break;
-        const bool dd = i <= z1;  // (d) of plane i in this iteration
+        const bool dd = i <= z1;  // plane i is one the tile needs (d) of
         // plane i - 3 was staged two iterations ago (and fenced): store it
         if (tst && tid == 0 && i >= z0 + 3) {
             tma_store_4d(&maps->out, outb + obuf(i - 3) * OSL, x0, y0, i - 3, 0);
@@ -595,18 +634,20 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         }
         const bool do_m = dd && i + PF <= z1, do_p = dd && i + 1 + PF <= z1 + 1;
         if (dd) {
-            // z mirror sign and inlet flag of plane i (its moments were loaded by
-            // the prologue or PF iterations ago)
-            inl_cur = 0;
-            resolve_axis(i, nz, P.face[4], P.face[5], sgz_cur, inl_cur);
             const int kb = bslot(i);
             if ((do_m || do_p) && issue(do_p, i + 1 + PF, do_m, i + PF, kb)) pend |= 1u << kb;
             if (!tma) cp_async_commit();
             wait_bar(bslot(i + 1));  // == bslot(i - PF)
         }
+        // z mirror sign and inlet flag of plane i
+        const float sgz_cur = i < 0 ? sgz_lo : (i >= nz ? sgz_hi : 1.f);
+        const bool inl_cur = inl_lo && i < 0;
+        // the output of (e) in this iteration (plane i - 2) is stored
+        const bool outA = storeA && i >= z0 + 2, outB = storeB && i >= z0 + 2;
 
         // (e) plane i - 1: y shift and moments, z shift and moments, output of plane i - 2
-        if (i >= z0) {
+        float2 avg_phi, avg_uz;  // the new phi and u_z of plane i - 2 (time averages)
+        {
             if constexpr (L::TC) {  // the handoffs of (d) of plane i - 1, parked in TMEM
                 float c[48];
 #pragma unroll
@@ -671,7 +712,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             cVP = h_vzp;
             if constexpr (L::TC) carries_store();
 
-            if (i >= z0 + 2) {  // (every lane computes; halo and out-of-grid lanes do not write)
+            {  // (every lane computes; halo and out-of-grid lanes, and planes before z0, do not write)
                 const float2 dr = O0[0], jx = O0[1], jy = O0[2], jz = O1[0];
                 const float2 rn = bc(1.f) + dr, irn = rcp2(rn);
                 const float2 ux = jx * irn, uy = jy * irn, uz = jz * irn;
@@ -690,56 +731,46 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                 val[F_PYZ] = O1[2] - ruy * uz;
                 val[F_PHI] = phin;
                 const long long zo = nxy * (i - 2);
-                if (tst) {  // into the staging box of plane i - 2: [field][tile row][tile column]
+                if constexpr (tst) {  // into the staging box of plane i - 2: [field][tile row][tile column]
                     float* ob = outb + obuf(i - 2) * OSL + (2 * w - 1) * TX + (lane - 1);
-                    if (storeA) {
+                    if (outA) {
 #pragma unroll
                         for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX] = val[f].x;
                     }
-                    if (storeB) {
+                    if (outB) {
 #pragma unroll
                         for (int f = 0; f < NFIELDS; ++f) ob[f * TY * TX + TX] = val[f].y;
                     }
                 } else {
-                    if (storeA) {
+                    if (outA) {
                         S* o = out + zo + sxyA;
 #pragma unroll
                         for (int f = 0; f < F_PHI; ++f) Io<S>::st(o + f * fs, val[f].x, P.scale[f]);
                         Io<S>::st_phi(o + F_PHI * fs, val[F_PHI].x, P.scale[F_PHI]);
                     }
-                    if (storeB) {
+                    if (outB) {
                         S* o = out + zo + sxyB;
 #pragma unroll
                         for (int f = 0; f < F_PHI; ++f) Io<S>::st(o + f * fs, val[f].y, P.scale[f]);
                         Io<S>::st_phi(o + F_PHI * fs, val[F_PHI].y, P.scale[F_PHI]);
                     }
                 }
-                if (storeA) {
+                if (outA) {
                     sum_rho += Io<S>::round_trip(dr.x, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
                     sum_phi += Io<S>::round_trip_phi(phin.x, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
-                if (storeB) {
+                if (outB) {
                     sum_rho += Io<S>::round_trip(dr.y, P.scale[F_DRHO], P.inv_scale[F_DRHO]);
                     sum_phi += Io<S>::round_trip_phi(phin.y, P.scale[F_PHI], P.inv_scale[F_PHI]);
                 }
-                if (P.avg) {  // time sums of the new phi and u_z (FP64)
-                    if (storeA) {
-                        double* a = P.avg + zo + sxyA;
-                        a[0] += (double)phin.x;
-                        a[fs] += (double)uz.x;
-                    }
-                    if (storeB) {
-                        double* a = P.avg + zo + sxyB;
-                        a[0] += (double)phin.y;
-                        a[fs] += (double)uz.y;
-                    }
-                }
+                avg_phi = phin;
+                avg_uz = uz;
             }
         }
 
         // (d) plane i: stencils, collision, x sweep, y populations -> y exchange of
         // plane i and the handoffs to its (e) in the next iteration
-        if (dd) {
+        {
             const S* mA = momb + mslot(i) * MSL + mrdA;
             const S* mB = momb + mslot(i) * MSL + mrdB;
             auto ld2 = [&](int f) {
@@ -751,13 +782,10 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             float2 ux = sgx * ld2(1), uy = sgy * ld2(2), uz = sgz_cur * ld2(3);
             const float2 pxx = ld2(4), pyy = ld2(5), pzz = ld2(6);
             const float2 pxy = (sgx * sgy) * ld2(7), pxz = (sgx * sgz_cur) * ld2(8), pyz = (sgz_cur * sgy) * ld2(9);
-            if (inl_cur) {
-                float ua[3], ub[3];
-                inlet_velocity(P, sx, syA, t, ua);
-                inlet_velocity(P, sx, syB, t, ub);
-                ux = make_float2(ua[0] * sgx, ub[0] * sgx);
-                uy = make_float2(ua[1] * sgyA, ub[1] * sgyB);
-                uz = make_float2(ua[2], ub[2]);
+            if constexpr (!L::kFp32) {
+                ux = inl_cur ? iux : ux;
+                uy = inl_cur ? iuy : uy;
+                uz = inl_cur ? iuz : uz;
             }
 
             // interface terms from the phase field of planes i - 1, i, i + 1 at
@@ -784,11 +812,9 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                     if (r == 1) phi.x = b;
                     if (r == 2) phi.y = b;
                 }
-                interface_nb(zS, zD, zL, lane, sig_half, P.normal_eps2, Fx, Fy, Fz, nxv, nyv, nzv);
-            }
-            if (inl_cur) {
-                Fx = Fy = Fz = bc(0.f);
-                nxv = nyv = nzv = bc(0.f);
+                // (the inlet ghost plane carries no interface terms)
+                interface_nb(zS, zD, zL, lane, sig_half, P.normal_eps2, Fx, Fy, Fz, nxv, nyv, nzv,
+                             inl_cur ? 0.f : 1.f);
             }
 
             // Guo forcing: v = u + F / (2 rho)
@@ -851,22 +877,33 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                 }
         }
 
-        if constexpr (L::TC) {
-            if (dd) {  // park this plane's handoffs in TMEM until its (e) in the next iteration
-                float c[48];
+        if constexpr (L::TC) {  // park this plane's handoffs in TMEM until its (e) in the next iteration
+            float c[48];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    c[2 * k] = hYZ[k].x, c[2 * k + 1] = hYZ[k].y;
-                    c[18 + k] = hPA[k];
-                    c[27 + k] = hMB[k];
-                }
-                c[36] = h_hx.x, c[37] = h_hx.y, c[38] = h_vzp.x, c[39] = h_vzp.y;
-                c[40] = h_vzm.x, c[41] = h_vzm.y, c[42] = h_dyA, c[43] = h_dyB;
+            for (int k = 0; k < 9; ++k) {
+                c[2 * k] = hYZ[k].x, c[2 * k + 1] = hYZ[k].y;
+                c[18 + k] = hPA[k];
+                c[27 + k] = hMB[k];
+            }
+            c[36] = h_hx.x, c[37] = h_hx.y, c[38] = h_vzp.x, c[39] = h_vzp.y;
+            c[40] = h_vzm.x, c[41] = h_vzm.y, c[42] = h_dyA, c[43] = h_dyB;
 #pragma unroll
-                for (int k = 44; k < 48; ++k) c[k] = 0.f;
+            for (int k = 44; k < 48; ++k) c[k] = 0.f;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) tmem_st8(tm_addr + 64u + 8u * k, c + 8 * k);
-                tmem_wait_st48(c);
+            for (int k = 0; k < 6; ++k) tmem_st8(tm_addr + 64u + 8u * k, c + 8 * k);
+            tmem_wait_st48(c);
+        }
+        if (P.avg && (outA || outB)) {  // time sums of the new phi and u_z of plane i - 2 (FP64)
+            const long long zo = nxy * (i - 2);
+            if (outA) {
+                double* a = P.avg + zo + sxyA;
+                a[0] += (double)avg_phi.x;
+                a[fs] += (double)avg_uz.x;
+            }
+            if (outB) {
+                double* a = P.avg + zo + sxyB;
+                a[0] += (double)avg_phi.y;
+                a[fs] += (double)avg_uz.y;
             }
         }
         // element-wise copies land by the end of the iteration that issued them
@@ -933,6 +970,14 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     return clean;
 }
 
+// Whether a tile's finished planes leave through the staging boxes: the
+// kernel form has them and the maps carry an output map for this block size.
+template <int NW, typename S, bool ST, bool WR>
+__device__ __forceinline__ bool staged_stores(const TileMaps* maps) {
+    return Step2Smem<NW, S, ST, WR>::kTmaStore && maps != nullptr && maps->valid && maps->block_warps == NW &&
+           maps->store;
+}
+
 // One time step of one grid: one block per tile.
 template <int NW, typename S, bool ST, bool WR>
 __global__ void __launch_bounds__(32 * NW, 1)
@@ -941,7 +986,14 @@ __global__ void __launch_bounds__(32 * NW, 1)
                  double* __restrict__ partials) {
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const long long t = *t_in;
-    step_tile<NW, S, ST, WR>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+    if constexpr (Step2Smem<NW, S, ST, WR>::kTmaStore) {
+        if (staged_stores<NW, S, ST, WR>(&M))
+            step_tile<NW, S, ST, WR, true>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+        else
+            step_tile<NW, S, ST, WR, false>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+    } else {
+        step_tile<NW, S, ST, WR, false>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+    }
     if (blk == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_out = t + 1;
 }
 
@@ -981,9 +1033,18 @@ __global__ void __launch_bounds__(32 * NW, 1)
         // the grid's tensor maps live in device memory, written before the launch
         const TileMaps* maps = &insts[tl.x].maps[parity];
         if (tid == 0) fence_tensormap_acquire(maps);
-        if (!step_tile<NW, float, ST, WR>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z, tl.w,
-                                          partials + 2 * k))
-            break;  // loads that never landed: take no further tile into this shared memory
+        bool clean;
+        if constexpr (Step2Smem<NW, float, ST, WR>::kTmaStore) {
+            clean = staged_stores<NW, float, ST, WR>(maps)
+                        ? step_tile<NW, float, ST, WR, true>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y,
+                                                             tl.z, tl.w, partials + 2 * k)
+                        : step_tile<NW, float, ST, WR, false>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y,
+                                                              tl.z, tl.w, partials + 2 * k);
+        } else {
+            clean = step_tile<NW, float, ST, WR, false>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z,
+                                                        tl.w, partials + 2 * k);
+        }
+        if (!clean) break;  // loads that never landed: take no further tile into this shared memory
     }
     if (blockIdx.x == 0 && tid == 0) *t_out = t + 1;
 }
