@@ -624,6 +624,9 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             iuz = make_float2(ua[2], ub[2]);
         }
     }
+    // (unrolled by two: the z carries and handoffs then pass between the two
+    // copies of the body by register renaming instead of moves)
+#pragma unroll 2
     for (int i = z0 - 1; i <= z1 + 1; ++i) {
         if (__syncthreads_or(dead)) break;
         const bool dd = i <= z1;  // plane i is one the tile needs (d) of
