@@ -561,6 +561,8 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     };
     if constexpr (L::TC) carries_store();
 
+    const unsigned msx = sgx < 0.f ? 0x80000000u : 0u, msyA = sgyA < 0.f ? 0x80000000u : 0u,
+                   msyB = sgyB < 0.f ? 0x80000000u : 0u;
     const float om1 = 1.f - P.omega, fo = 1.f - 0.5f * P.omega;
     const float sig_half = -0.5f * P.sigma;
 
@@ -780,11 +782,18 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                 return make_float2(Io<S>::cvt(mA[f * (WR ? fsA : FS)], P.inv_scale[f]),
                                    Io<S>::cvt(mB[f * (WR ? fsB : FS)], P.inv_scale[f]));
             };
-            const float2 sgy = make_float2(sgyA, sgyB);
+            // mirror images: the signs of the x, y, z velocity components and of
+            // the off-diagonal P components flip the FP32 sign bit (the ALU
+            // pipe, not the FMA pipe that the step is short of)
+            const unsigned mz = sgz_cur < 0.f ? 0x80000000u : 0u;
+            auto flip = [](float2 v, unsigned ma, unsigned mb) {
+                return make_float2(__uint_as_float(__float_as_uint(v.x) ^ ma), __uint_as_float(__float_as_uint(v.y) ^ mb));
+            };
             const float2 drho = ld2(0);
-            float2 ux = sgx * ld2(1), uy = sgy * ld2(2), uz = sgz_cur * ld2(3);
+            float2 ux = flip(ld2(1), msx, msx), uy = flip(ld2(2), msyA, msyB), uz = flip(ld2(3), mz, mz);
             const float2 pxx = ld2(4), pyy = ld2(5), pzz = ld2(6);
-            const float2 pxy = (sgx * sgy) * ld2(7), pxz = (sgx * sgz_cur) * ld2(8), pyz = (sgz_cur * sgy) * ld2(9);
+            const float2 pxy = flip(ld2(7), msx ^ msyA, msx ^ msyB), pxz = flip(ld2(8), msx ^ mz, msx ^ mz),
+                         pyz = flip(ld2(9), msyA ^ mz, msyB ^ mz);
             if constexpr (!L::kFp32) {
                 ux = inl_cur ? iux : ux;
                 uy = inl_cur ? iuy : uy;
