@@ -239,6 +239,22 @@ def test_departs_from_projection_closure_as_the_oracle_does():
 
 
 @pytest.mark.parametrize("block_warps", [8, 12])
+def test_plain_store_form_parity(block_warps):
+    """The plain-store form (the one the autotuner picks for this closure on
+    FP32 grids): parity with the oracle on every ghost rule of the jet, and on
+    ragged tiles with mirror faces."""
+    w = inputs.jet_workload(48, 40, 44, diameter=12, we=100, noise=0.01, seed=3)
+    check_parity(w, 100, plain_stores=True, block_warps=block_warps)
+    w = inputs.droplet_workload(8, radius=6.0)
+    w.nx, w.ny, w.nz = 36, 17, 29
+    w.faces = ("free_slip", "free_slip", "free_slip", "free_slip", "outflow", "outflow")
+    w.name = "ragged_mirror"
+    rho0, u0, _, _ = inputs.random_smooth_fields(36, 17, 29, seed=8, amp_rho=2e-3, amp_u=2e-2)
+    _, _, phi = inputs.droplet_fields(36, 17, 29, 6.0, 3.0, center=(13.0, 8.0, 15.0))
+    check_parity(w, 60, fields=(rho0, u0, phi), plain_stores=True, block_warps=block_warps)
+
+
+@pytest.mark.parametrize("block_warps", [8, 12])
 def test_staged_stores_equal_plain_stores(block_warps):
     """FP32 grids with 16-byte rows write finished planes through a staging box
     and one TMA store per plane; the plain-store form writes the same bits."""
