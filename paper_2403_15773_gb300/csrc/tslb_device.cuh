@@ -465,7 +465,8 @@ __device__ __forceinline__ void interface_x(const float2 (&yS)[3], const float2 
     const float2 hyz = s0v(yDD[0], yDD[1], yDD[2]);
 
     const float2 m2 = mad(gx, gx, mad(gy, gy, mad(gz, gz, bc(72.f * 72.f * eps2))));
-    const float2 im = keep * make_float2(m2.x > 0.f ? rsqrtf(m2.x) : 0.f, m2.y > 0.f ? rsqrtf(m2.y) : 0.f);
+    // (with eps = 0 a node without gradient has G = 0: the floor keeps im finite, so n = F = 0)
+    const float2 im = keep * make_float2(rsqrtf(fmaxf(m2.x, 1e-30f)), rsqrtf(fmaxf(m2.y, 1e-30f)));
     nxv = gx * im;
     nyv = gy * im;
     nzv = gz * im;

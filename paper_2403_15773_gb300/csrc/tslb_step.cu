@@ -163,12 +163,14 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     constexpr int EPT = L::EPT;
     constexpr int MSL = (int)(L::MOM_SLOT / sizeof(S)), PSL = (int)(L::PHI_SLOT / sizeof(S));
     constexpr int PF = L::PF, MS = L::MS, PS = L::PS, NB = L::NB;
-    // slots of plane q (q >= -2) and the mbarrier of the loads issued at iteration i (>= -1)
-    auto mslot = [](int q) { return (q + 12) % MS; };
-    auto pslot = [](int q) { return (q + 20) % PS; };
-    auto bslot = [](int i) { return (i + 12) % (PF + 1); };
-    // output staging box and y-exchange buffer of plane q
-    auto obuf = [](int q) { return (q + 8) & 1; };
+    // slots of plane q (q >= z0 - 2) and the mbarrier of the loads issued at
+    // iteration i (>= z0 - 1), counted from the tile's first plane so that the
+    // two copies of the unrolled march see fixed parities
+    auto mslot = [z0 = bz * P.tile_z](int q) { return (q - z0 + 12) % MS; };
+    auto pslot = [z0 = bz * P.tile_z](int q) { return (q - z0 + 20) % PS; };
+    auto bslot = [z0 = bz * P.tile_z](int i) { return (i - z0 + 12) % (PF + 1); };
+    // output staging box and y-exchange buffer of plane q (parity from z0)
+    auto obuf = [z0 = bz * P.tile_z](int q) { return (q - z0 + 8) & 1; };
     constexpr int BPRO = PF + 1;  // mbarrier of the prologue loads
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* const sm = align128(smem_raw);
