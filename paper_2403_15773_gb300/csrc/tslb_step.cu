@@ -80,8 +80,10 @@ struct Step2Smem {
     static constexpr bool kFp32 = sizeof(S) == 4;
     static constexpr int TXS = TX;
     // blocks of more than 12 warps keep the carries of the z march in tensor
-    // memory between planes (registers: 65536 / threads)
-    static constexpr bool TC = NW > 12 || (!kFp32 && NW > 8);
+    // memory between planes (registers: 65536 / threads); 12-warp blocks keep
+    // them in registers (the 16-bit form spills a little, and is still faster
+    // than with the round trips through tensor memory)
+    static constexpr bool TC = NW > 12;
     // box columns: staged columns x0-1 .. x0+30 (moments) and x0-2 .. x0+31
     // (phase field) from the 16-byte boundary below them
     static constexpr int MW = kFp32 ? 36 : 40;
