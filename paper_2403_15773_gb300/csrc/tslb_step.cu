@@ -683,12 +683,16 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const int k = 3 * qx + c;
-                    const float2 qp = make_float2(yprev[(2 * k) * NT], hPA[k]);
-                    const float2 qm = make_float2(hMB[k], ynext[(2 * k + 1) * NT]);
-                    const float2 s = qp + qm;
-                    Y[qx][0][c] = s + hYZ[k];
-                    Y[qx][1][c] = qp - qm;
-                    Y[qx][2][c] = s;
+                    if (!L::kFp32 && qx == 2) {  // zeroth y moment only (16-bit forms; see (d))
+                        Y[qx][0][c] = make_float2(yprev[(2 * k) * NT], ynext[(2 * k + 1) * NT]) + hYZ[k];
+                    } else {
+                        const float2 qp = make_float2(yprev[(2 * k) * NT], hPA[k]);
+                        const float2 qm = make_float2(hMB[k], ynext[(2 * k + 1) * NT]);
+                        const float2 s = qp + qm;
+                        Y[qx][0][c] = s + hYZ[k];
+                        Y[qx][1][c] = qp - qm;
+                        Y[qx][2][c] = s;
+                    }
                 }
             const float2 hxy = mad(0.125f, make_float2(yprev[18 * NT], h_dyB) + make_float2(h_dyA, ynext[19 * NT]), h_hx);
 
@@ -887,9 +891,16 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
                     const int k = 3 * qx + c;
                     yb[(2 * k) * NT] = tr.p.y;
                     yb[(2 * k + 1) * NT] = tr.m.x;
-                    hYZ[k] = tr.z;
-                    hPA[k] = tr.p.x;
-                    hMB[k] = tr.m.y;
+                    if (!L::kFp32 && qx == 2) {
+                        // (16-bit forms, short of registers) x moment 2 needs only the zeroth
+                        // y moment: the own rows' part of it is handed over as one sum
+                        hYZ[k] = make_float2(tr.z.x + tr.m.y, tr.z.y + tr.p.x);
+                        hPA[k] = hMB[k] = 0.f;
+                    } else {
+                        hYZ[k] = tr.z;
+                        hPA[k] = tr.p.x;
+                        hMB[k] = tr.m.y;
+                    }
                 }
         }
 
