@@ -225,25 +225,46 @@ def oracle_sample_workload(w, dims=(64, 64, 32)):
     return w
 
 
-def cpu_baseline(w, budget_s: float = 12.0):
+def _oracle_rate(s_w, budget_s: float):
+    """GLUPS of the FP64 oracle on workload s_w (steps fitted to about budget_s), steps, seconds."""
     import oracle
-    s_w = oracle_sample_workload(w)
     sim = oracle.OracleSim(oracle_params_of(s_w))
     rho, u, phi = s_w.fields()
     sim.set_state(rho, u, phi)
     sim.step(1)                     # the first step also starts the thread pool
     t0 = time.perf_counter()
-    sim.step(3)
-    one = (time.perf_counter() - t0) / 3
+    sim.step(2)
+    one = (time.perf_counter() - t0) / 2
     n = max(1, min(1000, int(budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
     sim.step(n)
     dt = time.perf_counter() - t0
-    glups = s_w.nodes * n / dt / 1e9
-    return {"value": glups, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"FP64 oracle (paper-literal 27+7 population push), {n} steps of a "
-                      f"{s_w.nx}x{s_w.ny}x{s_w.nz} crop of the workload around the nozzle, "
-                      f"{dt:.1f} s"}
+    return s_w.nodes * n / dt / 1e9, n, dt
+
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    """The oracle on the host cores: the headline figure on a crop of the
+    workload around the nozzle with every core, and beside it the same crop on
+    one thread and the 32^3 static droplet in full (every core)."""
+    import oracle
+    from paper_2403_15773_gb300 import inputs
+    s_w = oracle_sample_workload(w)
+    glups, n, dt = _oracle_rate(s_w, budget_s)
+    crop = f"{s_w.nx}x{s_w.ny}x{s_w.nz} crop of the workload around the nozzle"
+    cores = oracle.threads()
+    out = {"value": glups, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"FP64 oracle (paper-literal 27+7 population push), {n} steps of a {crop}, {dt:.1f} s"}
+    try:
+        oracle.set_threads(1)
+        g1, n1, dt1 = _oracle_rate(s_w, budget_s / 4)
+    finally:
+        oracle.set_threads(cores)
+    out["single_thread"] = {"value": g1, "unit": UNIT, "cores": 1, "sample": f"{n1} steps of the {crop}, {dt1:.1f} s"}
+    d = inputs.droplet_workload()
+    gd, nd, dtd = _oracle_rate(d, budget_s / 4)
+    out["droplet32"] = {"value": gd, "unit": UNIT, "cores": cores,
+                        "sample": f"{nd} steps of the periodic {d.nx}^3 static droplet in full, {dtd:.1f} s"}
+    return out
 
 
 # ------------------------------------------------------------- multi-rank

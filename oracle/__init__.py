@@ -88,6 +88,8 @@ def lib():
             l.orc_time.argtypes = [ctypes.c_void_p]
             l.orc_time.restype = ctypes.c_int64
             l.orc_threads.restype = ctypes.c_int
+            l.orc_set_threads.argtypes = [ctypes.c_int]
+            l.orc_set_threads.restype = None
             l.orc_step_sample.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _D, _D, _D, _D,
                                           ctypes.c_int64, _I64, _D]
             l.orc_step_sample.restype = ctypes.c_int
@@ -245,3 +247,8 @@ def inlet_state(params: Params, x: int, y: int, t: int):
 
 def threads() -> int:
     return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the later steps (timing only: the results do not depend on it)."""
+    lib().orc_set_threads(int(n))

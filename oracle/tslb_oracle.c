@@ -478,6 +478,14 @@ int orc_threads(void) {
 #endif
 }
 
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_set_state(orc_sim* s, const double* rho, const double* u, const double* pi,
                   const double* phi, int64_t t0) {
     tables();

@@ -69,6 +69,8 @@ void orc_get_moments(const orc_sim* s, double* rho, double* u, double* pi, doubl
 void orc_sums(const orc_sim* s, double* mass, double* phi_total, double* momentum3);
 int64_t orc_time(const orc_sim* s);
 int orc_threads(void);
+/* Threads of the later steps (n >= 1; timing only: the results do not depend on it). */
+void orc_set_threads(int n);
 
 /* One step evaluated only at the listed nodes, from a full stored state
  * (rho, u, pi, phi over the whole grid at step t).  out: 11 values per sample

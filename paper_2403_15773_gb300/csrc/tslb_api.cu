@@ -3,6 +3,7 @@
 // I/O, graph-captured time stepping, FP64 sums, checkpoints and the tile-shape
 // autotuner.  All compute runs in the kernels of tslb_step.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -18,6 +19,16 @@
 using tslb::StepParams;
 
 namespace {
+
+// A named range on the profiler timeline (NVTX) around an entry point's host
+// side (the GPU work it enqueues runs later, on the context's stream);
+// without a profiler attached the push and pop do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // One grid of a context: its parameters, node count and its two state buffers.
 struct Instance {
@@ -836,12 +847,14 @@ size_t tslb_batch_workspace_bytes(int32_t count, const tslb_grid* grids, const t
 
 tslb_status tslb_init(tslb_ctx** out, const tslb_grid* grid, tslb_lattice lattice, double omega, double sigma,
                       const tslb_boundary* bc, const tslb_options* opt, void* workspace, size_t workspace_bytes) {
+    const NvtxRange r("tslb_init");
     return create(out, 1, grid, lattice, &omega, &sigma, bc, opt, workspace, workspace_bytes, false);
 }
 
 tslb_status tslb_init_batch(tslb_ctx** out, int32_t count, const tslb_grid* grids, tslb_lattice lattice,
                             const double* omega, const double* sigma, const tslb_boundary* bcs,
                             const tslb_options* opt, void* workspace, size_t workspace_bytes) {
+    const NvtxRange r("tslb_init_batch");
     return create(out, count, grids, lattice, omega, sigma, bcs, opt, workspace, workspace_bytes, count > 1);
 }
 
@@ -861,6 +874,7 @@ tslb_status tslb_batch_set_state(tslb_ctx* c, int32_t instance, const float* rho
 }
 
 tslb_status tslb_step(tslb_ctx* c, int64_t n) {
+    const NvtxRange r("tslb_step");
     if (!c) return TSLB_ERR_INVALID_ARG;
     if (n < 0) return bad(c, "n must be >= 0");
     if (!all_set(c)) return bad(c, "tslb_step before the state of every grid is set", TSLB_ERR_STATE);
@@ -941,6 +955,7 @@ tslb_status tslb_sums(tslb_ctx* c, double* mass, double* phi_total) {
 }
 
 tslb_status tslb_batch_sums(tslb_ctx* c, int32_t instance, double* mass, double* phi_total) {
+    const NvtxRange r("tslb_sums");
     if (!c) return TSLB_ERR_INVALID_ARG;
     if (!mass || !phi_total) return bad(c, "mass and phi_total are required");
     tslb_status s = check_instance(c, instance);
@@ -980,6 +995,7 @@ std::vector<int> slab_candidates(const tslb_ctx* c, int nw) {
 
 tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z,
                           int32_t* plain_stores) {
+    const NvtxRange r("tslb_autotune");
     if (!c) return TSLB_ERR_INVALID_ARG;
     if (steps_per_trial < 1) return bad(c, "steps_per_trial must be >= 1");
     if (!all_set(c)) return bad(c, "tslb_autotune before the state of every grid is set", TSLB_ERR_STATE);

@@ -469,3 +469,28 @@ def test_inlet_and_outflow_ghosts_equal_explicit_planes(case):
     plain.step(1)
     c = plain.moments()
     assert np.max(np.abs(a[0][0] - c[0][0])) > 1e-5 and np.max(np.abs(a[0][-1] - c[0][-1])) > 1e-5
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The oracle updates every node independently and sums in a fixed order,
+    so the thread count (which the benchmark varies for its timing) changes
+    no bit of the state or the totals."""
+    w = inputs.droplet_workload(12, radius=4.0)
+    rho, u, pi, _ = inputs.random_smooth_fields(12, 12, 12, seed=17, amp_rho=1e-2, amp_u=1e-2, amp_pi=5e-4)
+    _, _, phi = inputs.droplet_fields(12, 12, 12, 4.0, 3.0)
+    n0 = oracle.threads()
+    out = []
+    try:
+        for n in (1, max(2, n0)):
+            oracle.set_threads(n)
+            s = oracle.OracleSim(oracle_params(w))
+            s.set_state(rho, u, phi, pi=pi)
+            s.step(5)
+            out.append((s.moments(), s.sums()))
+    finally:
+        oracle.set_threads(n0)
+    (m1, s1), (m2, s2) = out
+    for a, b in zip(m1, m2):
+        assert np.array_equal(a, b)
+    for a, b in zip(s1, s2):
+        assert np.array_equal(a, b)
