@@ -29,7 +29,7 @@ __all__ = [
     "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
     "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
     "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
-    "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate", "tslb_halo_values", "tslb_halo_pack",
+    "tslb_step_form", "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate", "tslb_halo_values", "tslb_halo_pack",
     "tslb_halo_unpack", "Simulation", "BatchSimulation", "SYMBOLS",
 ]
 
@@ -46,7 +46,7 @@ SYMBOLS = ("tslb_default_options", "tslb_workspace_bytes", "tslb_init", "tslb_se
            "tslb_status_string", "tslb_kernel_launches", "tslb_field_sums_noalloc",
            "tslb_batch_workspace_bytes", "tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments",
            "tslb_batch_get_phi", "tslb_batch_sums", "tslb_batch_count", "tslb_autotune",
-           "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate", "tslb_halo_values",
+           "tslb_step_form", "tslb_get_averages", "tslb_reset_averages", "tslb_fp32_lane_rate", "tslb_halo_values",
            "tslb_halo_pack", "tslb_halo_unpack")
 
 
@@ -67,7 +67,7 @@ class Options(ctypes.Structure):
                 ("graph_steps", ctypes.c_int32), ("block_warps", ctypes.c_int32),
                 ("scheme", ctypes.c_int32), ("average", ctypes.c_int32), ("closure", ctypes.c_int32),
                 ("test_tma_stall", ctypes.c_int32), ("plain_stores", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("per_tile_loads", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
 class TslbError(RuntimeError):
@@ -129,6 +129,8 @@ def lib() -> ctypes.CDLL:
             L.tslb_batch_count.argtypes = [VP]
             L.tslb_batch_count.restype = ctypes.c_int32
             L.tslb_autotune.argtypes = [VP, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]
+            L.tslb_step_form.argtypes = [VP, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
+                                         P(ctypes.c_int32)]
             L.tslb_get_averages.argtypes = [VP, ctypes.c_int32, VP, VP, P(ctypes.c_int64), ctypes.c_int]
             L.tslb_get_averages.restype = ctypes.c_int
             L.tslb_reset_averages.argtypes = [VP]
@@ -142,7 +144,7 @@ def lib() -> ctypes.CDLL:
             L.tslb_halo_unpack.argtypes = [VP, ctypes.c_int32, VP, ctypes.c_int]
             L.tslb_halo_unpack.restype = ctypes.c_int
             for name in ("tslb_init_batch", "tslb_batch_set_state", "tslb_batch_get_moments", "tslb_batch_get_phi",
-                         "tslb_batch_sums", "tslb_autotune"):
+                         "tslb_batch_sums", "tslb_autotune", "tslb_step_form"):
                 getattr(L, name).restype = ctypes.c_int
             for name in ("tslb_init", "tslb_set_state", "tslb_step", "tslb_get_moments", "tslb_get_phi",
                          "tslb_sums", "tslb_get_time", "tslb_get_state", "tslb_put_state",
@@ -290,6 +292,14 @@ def tslb_batch_count(ctx: int) -> int:
     return int(lib().tslb_batch_count(ctx))
 
 
+def tslb_step_form(ctx: int):
+    """The step kernel form of the next step: (block_warps, tile_z,
+    plain_stores, tma_only)."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().tslb_step_form(ctx, *(ctypes.byref(x) for x in v)), ctx)
+    return tuple(x.value for x in v)
+
+
 def tslb_autotune(ctx: int, steps_per_trial: int = 8):
     """Returns the chosen (block_warps, tile_z, plain_stores)."""
     nw, tz, pl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -356,7 +366,7 @@ class Simulation:
     def __init__(self, workload, storage: str = "fp32", stream=None, tile_z: int = 0,
                  graph_steps: int = 0, check_every: int = 0, field_scale=None, block_warps: int = 0,
                  average: bool = False, scheme: str = "fused", closure: str = "projection",
-                 test_tma_stall: int = 0, plain_stores: bool = False):
+                 test_tma_stall: int = 0, plain_stores: bool = False, per_tile_loads: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Simulation needs a CUDA device")
@@ -377,6 +387,7 @@ class Simulation:
         o.closure = CLOSURES[closure]
         o.test_tma_stall = int(test_tma_stall)
         o.plain_stores = 1 if plain_stores else 0
+        o.per_tile_loads = 1 if per_tile_loads else 0
         self.closure = closure
         if field_scale is not None:
             for g in range(4):
@@ -487,6 +498,11 @@ class Simulation:
         """Pick the fastest kernel form (block size, store path) and slab depth;
         the state is unchanged.  Returns (block_warps, tile_z, plain_stores)."""
         return tslb_autotune(self.ctx, steps_per_trial)
+
+    def step_form(self):
+        """(block_warps, tile_z, plain_stores, tma_only) of the next step's
+        kernel; tma_only: the kernel compiled for TMA tile loads alone."""
+        return tslb_step_form(self.ctx)
 
     def averages(self):
         """Time averages (<phi>, <u_z>) as float64 numpy arrays shaped like the

@@ -79,6 +79,8 @@ struct tslb_ctx {
     int64_t avg_steps = 0;
     int scheme = 0;          // 0 fused moment-only step, 1 the paper's two-sweep design
     float* pops = nullptr;   // scheme 1: 34 population arrays
+    bool tma12[2] = {false, false};  // every tile loads by TMA in the 12-warp form, without / with the
+                                     // periodic-face side boxes (tslb::tiles_all_tma at set-up)
     std::string err;
 };
 
@@ -219,6 +221,10 @@ bool make_params(const tslb_grid* grid, double omega, double sigma, const tslb_b
     }
     if (opt->plain_stores != 0 && opt->plain_stores != 1) {
         why = "plain_stores must be 0 or 1";
+        return false;
+    }
+    if (opt->per_tile_loads != 0 && opt->per_tile_loads != 1) {
+        why = "per_tile_loads must be 0 or 1";
         return false;
     }
     if (b.face[4] == TSLB_BC_INLET && !(b.inlet_diameter >= 0.f)) {
@@ -439,6 +445,23 @@ tslb_status upload_batch(tslb_ctx* c) {
     return TSLB_OK;
 }
 
+// The tensor maps of a single grid's projection step from parity q, made
+// for the current block size if they were made for another one, with
+// all_tma set where the 12-warp form may run the kernel compiled for TMA
+// tile loads alone.
+cudaError_t single_maps(tslb_ctx* c, int q, tslb::TileMaps** out) {
+    Instance& I = c->inst[0];
+    tslb::TileMaps& m = I.maps[q];
+    if (m.block_warps != I.p.block_warps) {  // boxes are shaped for one block size
+        cudaError_t e = tslb::make_tile_maps(I.p, c->storage, I.buf[q], I.buf[q ^ 1], &m);
+        if (e != cudaSuccess) return e;
+        m.block_warps = I.p.block_warps;
+    }
+    m.all_tma = m.valid && I.p.block_warps == 12 && c->tma12[m.wrap ? 1 : 0] ? 1 : 0;
+    *out = &m;
+    return cudaSuccess;
+}
+
 // One time step from parity q (state buf[q], step counter tdev[q]) to q ^ 1.
 cudaError_t launch_one(tslb_ctx* c, int q) {
     if (c->scheme == 1) {
@@ -459,14 +482,11 @@ cudaError_t launch_one(tslb_ctx* c, int q) {
     }
     if (!c->batch) {
         Instance& I = c->inst[0];
-        tslb::TileMaps& m = I.maps[q];
-        if (m.block_warps != I.p.block_warps) {  // boxes are shaped for one block size
-            cudaError_t e = tslb::make_tile_maps(I.p, c->storage, I.buf[q], I.buf[q ^ 1], &m);
-            if (e != cudaSuccess) return e;
-            m.block_warps = I.p.block_warps;
-        }
+        tslb::TileMaps* m = nullptr;
+        cudaError_t e = single_maps(c, q, &m);
+        if (e != cudaSuccess) return e;
         return tslb::launch_step(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
-                                 c->partials, c->stream, &m);
+                                 c->partials, c->stream, m);
     }
     return tslb::launch_batch_step(c->batch_nw, c->batch_plain, c->batch_wrap, c->dinst, c->dtiles, c->ntiles, q,
                                    c->tdev + q, c->tdev + (q ^ 1), c->counters, c->partials, c->sms, c->stream);
@@ -542,6 +562,9 @@ tslb_status finish_sums(tslb_ctx* c, int i, double* mass, double* phi_total) {
     CK(cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream), "sums copy");
     CK(cudaMemcpyAsync(&err, c->counters + 2, sizeof(err), cudaMemcpyDeviceToHost, c->stream), "error word copy");
     CK(cudaStreamSynchronize(c->stream), "sums synchronise");
+    if (err == 2)
+        return bad(c, "internal: a step kernel compiled for TMA tile loads met a tile that loads element by element",
+                   TSLB_ERR_CUDA);
     if (err) return bad(c, "a step kernel gave up waiting for its tile data (bounded wait expired)", TSLB_ERR_TIMEOUT);
     *mass = (double)I.N + r[0];
     *phi_total = r[1];
@@ -694,7 +717,8 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
     c->max_tiles = L.max_tiles;
     c->result = reinterpret_cast<double*>(base + L.result);
     c->tdev = reinterpret_cast<long long*>(base + L.tdev);
-    c->counters = reinterpret_cast<int*>(base + L.counters);  // [0..1] batch tile counters, [2] error word
+    c->counters = reinterpret_cast<int*>(base + L.counters);  // [0..1] batch tile counters, [2] error word,
+                                                               // [3] tile classification flag
     for (Instance& I : c->inst) I.p.err = c->counters + 2;
     c->dinst = reinterpret_cast<tslb::BatchInstance*>(base + L.dinst);
     c->dtiles = reinterpret_cast<int4*>(base + L.dtiles);
@@ -710,6 +734,17 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
     if (batch) {
         tslb_status s = upload_batch(c);
         if (s != TSLB_OK) return fail(s);
+    } else if (c->scheme == 0 && !o.per_tile_loads) {
+        // which grids the step kernel compiled for TMA tile loads alone may run
+        const StepParams& p = c->inst[0].p;
+        const bool periodic = p.face[0] == tslb::BC_PERIODIC || p.face[2] == tslb::BC_PERIODIC;
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+            if (w == 0 || (periodic && c->storage == TSLB_FP32))
+                e = tslb::tiles_all_tma(p, c->storage, w == 1, c->counters + 3, c->stream, &c->tma12[w]);
+        if (e != cudaSuccess) {
+            c->err = std::string("tile classification: ") + cudaGetErrorString(e);
+            return fail(TSLB_ERR_CUDA);
+        }
     }
     *out = c;
     return TSLB_OK;
@@ -1092,6 +1127,25 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
     if (tile_z) *tile_z = best_tz;
     if (plain_stores) *plain_stores = best_plain ? 1 : 0;
     return st;
+}
+
+tslb_status tslb_step_form(tslb_ctx* c, int32_t* block_warps, int32_t* tile_z, int32_t* plain_stores,
+                           int32_t* tma_only) {
+    if (!c) return TSLB_ERR_INVALID_ARG;
+    if (c->batch) return bad(c, "the step form is reported for single-grid contexts");
+    const Instance& I = c->inst[0];
+    bool to = false;
+    if (c->scheme == 0 && I.p.closure == tslb::CL_PROJECTION) {
+        CK(cudaSetDevice(c->device), "set device");
+        tslb::TileMaps* m = nullptr;
+        CK(single_maps(c, c->cur, &m), "tensor maps");
+        to = m->all_tma && I.p.plain_stores == 0;
+    }
+    if (block_warps) *block_warps = I.p.block_warps;
+    if (tile_z) *tile_z = I.p.tile_z;
+    if (plain_stores) *plain_stores = I.p.plain_stores;
+    if (tma_only) *tma_only = to ? 1 : 0;
+    return TSLB_OK;
 }
 
 size_t tslb_state_bytes(const tslb_ctx* c) {

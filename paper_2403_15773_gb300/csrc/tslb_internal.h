@@ -74,6 +74,8 @@ struct TileMaps {
     int store;
     int wrap;
     int block_warps;
+    int all_tma;  // every tile of the grid loads by TMA (tiles_all_tma): 12-warp blocks with
+                  // staged stores run the step kernel compiled for that load path alone
 };
 
 
@@ -107,6 +109,13 @@ cudaError_t launch_step(const StepParams& p, int storage, const void* in, void* 
 // blocks of p.block_warps warps (maps->valid = 0 where TMA cannot address the
 // layout: rows not a multiple of 16 bytes).  Host only; needs no device work.
 cudaError_t make_tile_maps(const StepParams& p, int storage, const void* in, const void* out, TileMaps* maps);
+
+// Whether every tile of grid p loads by TMA in the 12-warp staged-store form
+// of the step kernel (with the periodic-face side boxes if wrap; FP32 only):
+// the kernel's own tile set-up, run once per x-y tile, ORs a refusal into
+// *flag (one device int, scratch).  Synchronises stream s; not for use while
+// it is being captured.  *all = false for other closures.
+cudaError_t tiles_all_tma(const StepParams& p, int storage, bool wrap, int* flag, cudaStream_t s, bool* all);
 
 // Kernel attributes (dynamic shared memory) of the step kernel; once per device.
 cudaError_t prepare_kernels(int storage);

@@ -154,7 +154,15 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 // planes do leave through the staging boxes (a kernel form with them, and
 // maps with the output map: staged_stores()); a compile-time flag, so that
 // the march has no branch on it.
-template <int NW, typename S, bool ST, bool WR, bool TS>
+// MODE: TILE_ANY chooses the load path per tile at run time; TILE_TMA is
+// compiled for TMA loads alone (no element-wise path in the march: fewer
+// registers and instructions), for launches whose tiles all load by TMA;
+// TILE_CLASSIFY stops after the set-up and returns whether this tile can load
+// by TMA (tile_class_kernel).  The last two exist for blocks of at most 12
+// warps (no tensor-memory carries).
+constexpr int TILE_ANY = 0, TILE_TMA = 1, TILE_CLASSIFY = 2;
+
+template <int NW, typename S, bool ST, bool WR, bool TS, int MODE = TILE_ANY>
 __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
                                           S* __restrict__ out, const long long t, const int bx, const int by,
                                           const int bz, double* __restrict__ part) {
@@ -191,8 +199,9 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     const bool use_maps = maps != nullptr && maps->valid && maps->block_warps == NW;
     // finished planes leave through the staging box by TMA store (FP32)
     static_assert(!TS || L::kTmaStore, "staged stores need the staging boxes");
+    static_assert(MODE == TILE_ANY || !L::TC, "TMA-only and classification forms: blocks of at most 12 warps");
     constexpr bool tst = TS;
-    if (use_maps && tid == 0) {
+    if (MODE != TILE_CLASSIFY && use_maps && tid == 0) {
         for (int k = 0; k < NB; ++k) mbar_init(bar + k, 1);
         fence_mbar_init();
     }
@@ -338,20 +347,26 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
         if (w == 0) tmem_alloc(tm_slot, L::TM_COLS);
         tmem_fence_before();
     }
-    const bool tma = __syncthreads_and(use_maps && inbox && (!WR || !(wrx || wry) || maps->wrap)) != 0;
+    const bool tma_ok = __syncthreads_and(use_maps && inbox && (!WR || !(wrx || wry) || maps->wrap)) != 0;
+    if constexpr (MODE == TILE_CLASSIFY) return tma_ok;
+    // TILE_TMA: the host launches this form only where every tile loads by
+    // TMA.  A tile that cannot (not met) still loads its boxes, reads at its
+    // own box positions (all inside shared memory), and reports error 2.
+    if (MODE == TILE_TMA && !tma_ok && tid == 0 && P.err) *P.err = 2;
+    const bool tma = MODE == TILE_TMA || tma_ok;  // a constant in the TILE_TMA form
     if constexpr (L::TC) {
         tmem_fence_after();
         tm_base = *tm_slot;
         tm_addr = tm_base + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(w >> 2) * 128u;
     }
-    if (tma) {
+    if (tma && tma_ok) {
         if constexpr (!WR) {  // (WR: mrdA / mrdB set above)
             mrdA = resA;
             mrdB = resB;
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) rd4[r] = res4[r];
-    } else if constexpr (WR) {  // element-wise after all: own positions, box stride
+    } else if constexpr (WR) {  // element-wise after all (or TILE_TMA, not met): own positions, box stride
         mrdA = (2 * w) * MW + lane + offm;
         mrdB = mrdA + MW;
         fsA = fsB = FS;
@@ -1005,23 +1020,42 @@ __device__ __forceinline__ bool staged_stores(const TileMaps* maps) {
            maps->store;
 }
 
-// One time step of one grid: one block per tile.
-template <int NW, typename S, bool ST, bool WR>
+// One time step of one grid: one block per tile.  TO: every tile of the
+// grid loads by TMA (tile_class_kernel said so), the march is compiled for
+// that path alone.
+template <int NW, typename S, bool ST, bool WR, bool TO = false>
 __global__ void __launch_bounds__(32 * NW, 1)
     step2_kernel(const __grid_constant__ StepParams P, const __grid_constant__ TileMaps M, const S* __restrict__ in,
                  S* __restrict__ out, const long long* __restrict__ t_in, long long* __restrict__ t_out,
                  double* __restrict__ partials) {
+    constexpr int MODE = TO ? TILE_TMA : TILE_ANY;
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const long long t = *t_in;
     if constexpr (Step2Smem<NW, S, ST, WR>::kTmaStore) {
         if (staged_stores<NW, S, ST, WR>(&M))
-            step_tile<NW, S, ST, WR, true>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+            step_tile<NW, S, ST, WR, true, MODE>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                 partials + 2 * blk);
         else
-            step_tile<NW, S, ST, WR, false>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+            step_tile<NW, S, ST, WR, false, MODE>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                  partials + 2 * blk);
     } else {
-        step_tile<NW, S, ST, WR, false>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z, partials + 2 * blk);
+        step_tile<NW, S, ST, WR, false, MODE>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
+                                              partials + 2 * blk);
     }
     if (blk == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_out = t + 1;
+}
+
+// Tile classification: each block runs the set-up of its tile in the step
+// kernel form <NW, S, ST, WR> (x-y tile (blockIdx.x, blockIdx.y); the choice
+// does not depend on z) and ORs 1 into *flag if that tile would load element
+// by element.  M: maps flags only (valid, block_warps, wrap); the choice
+// depends on the grid, its faces and the box shapes, not on the buffers.
+template <int NW, typename S, bool ST, bool WR>
+__global__ void __launch_bounds__(32 * NW, 1)
+    tile_class_kernel(const __grid_constant__ StepParams P, const __grid_constant__ TileMaps M, int* __restrict__ flag) {
+    const bool ok =
+        step_tile<NW, S, ST, WR, false, TILE_CLASSIFY>(P, &M, nullptr, nullptr, 0, blockIdx.x, blockIdx.y, 0, nullptr);
+    if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(flag, 1);
 }
 
 // One time step of a batch of independent grids in one persistent launch:
@@ -1182,7 +1216,7 @@ int conv_blocks(const StepParams& p) {
     return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
 }
 
-template <int NW, typename S, bool ST, bool WR>
+template <int NW, typename S, bool ST, bool WR, bool TO = false>
 cudaError_t launch_nw(const StepParams& p, int storage, const void* in, void* out, const long long* t_in,
                       long long* t_out, double* partials, cudaStream_t s, const TileMaps* maps) {
     const LaunchShape sh = step_shape(p, storage);
@@ -1191,7 +1225,7 @@ cudaError_t launch_nw(const StepParams& p, int storage, const void* in, void* ou
         memset(&none, 0, sizeof(none));
         maps = &none;
     }
-    step2_kernel<NW, S, ST, WR><<<sh.grid, sh.block, Step2Smem<NW, S, ST, WR>::BYTES, s>>>(
+    step2_kernel<NW, S, ST, WR, TO><<<sh.grid, sh.block, Step2Smem<NW, S, ST, WR>::BYTES, s>>>(
         p, *maps, static_cast<const S*>(in), static_cast<S*>(out), t_in, t_out, partials);
     return cudaGetLastError();
 }
@@ -1199,6 +1233,8 @@ cudaError_t launch_nw(const StepParams& p, int storage, const void* in, void* ou
 template <typename S>
 cudaError_t launch_step_t(const StepParams& p, int st, const void* in, void* out, const long long* t_in,
                           long long* t_out, double* partials, cudaStream_t s, const TileMaps* m) {
+    // 12 warps, staged stores: the TMA-only form where every tile loads by TMA
+    const bool to = m && m->valid && m->all_tma && p.block_warps == 12 && p.plain_stores == 0;
     if constexpr (sizeof(S) == 4) {  // FP32 blocks of 8 or 12 warps: plain-store and periodic-face forms
         const bool pl = p.plain_stores != 0, wr = m && m->valid && m->wrap;
         if (p.block_warps == 8) {
@@ -1207,25 +1243,44 @@ cudaError_t launch_step_t(const StepParams& p, int st, const void* in, void* out
             if (pl) return launch_nw<8, S, false, false>(p, st, in, out, t_in, t_out, partials, s, m);
         }
         if (p.block_warps == 12) {
-            if (wr) return pl ? launch_nw<12, S, false, true>(p, st, in, out, t_in, t_out, partials, s, m)
-                              : launch_nw<12, S, true, true>(p, st, in, out, t_in, t_out, partials, s, m);
+            if (wr) return pl   ? launch_nw<12, S, false, true>(p, st, in, out, t_in, t_out, partials, s, m)
+                           : to ? launch_nw<12, S, true, true, true>(p, st, in, out, t_in, t_out, partials, s, m)
+                                : launch_nw<12, S, true, true>(p, st, in, out, t_in, t_out, partials, s, m);
             if (pl) return launch_nw<12, S, false, false>(p, st, in, out, t_in, t_out, partials, s, m);
         }
         if (p.block_warps == 16 && pl) return launch_nw<16, S, false, false>(p, st, in, out, t_in, t_out, partials, s, m);
     }
     switch (p.block_warps) {
         case 8: return launch_nw<8, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
-        case 12: return launch_nw<12, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
+        case 12: return to ? launch_nw<12, S, true, false, true>(p, st, in, out, t_in, t_out, partials, s, m)
+                           : launch_nw<12, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
         case 14: return launch_nw<14, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
         case 16: return launch_nw<16, S, true, false>(p, st, in, out, t_in, t_out, partials, s, m);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int NW, typename S, bool ST, bool WR>
+template <int NW, typename S, bool ST, bool WR, bool TO = false>
 cudaError_t prepare_nw() {
-    return cudaFuncSetAttribute(step2_kernel<NW, S, ST, WR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(step2_kernel<NW, S, ST, WR, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Step2Smem<NW, S, ST, WR>::BYTES);
+}
+
+// Whether every tile of the grid loads by TMA in the 12-warp staged-store
+// form (with side boxes if WR): one tile_class_kernel launch into *flag.
+template <typename S, bool WR>
+cudaError_t classify_t(const StepParams& p, int storage, int* flag, cudaStream_t s) {
+    StepParams q = p;
+    q.block_warps = 12;
+    q.plain_stores = 0;
+    const LaunchShape sh = step_shape(q, storage);
+    TileMaps m;
+    memset(&m, 0, sizeof(m));
+    m.valid = 1;
+    m.block_warps = 12;
+    m.wrap = WR ? 1 : 0;
+    tile_class_kernel<12, S, true, WR><<<dim3(sh.grid.x, sh.grid.y, 1), dim3(32, 12, 1), 0, s>>>(q, m, flag);
+    return cudaGetLastError();
 }
 
 template <int NW, bool ST, bool WR>
@@ -1241,6 +1296,7 @@ template <typename S>
 cudaError_t prepare_t() {
     cudaError_t e = prepare_nw<8, S, true, false>();
     if (e == cudaSuccess) e = prepare_nw<12, S, true, false>();
+    if (e == cudaSuccess) e = prepare_nw<12, S, true, false, true>();
     if (e == cudaSuccess) e = prepare_nw<14, S, true, false>();
     if (e == cudaSuccess) e = prepare_nw<16, S, true, false>();
     if constexpr (sizeof(S) == 4) {
@@ -1249,6 +1305,7 @@ cudaError_t prepare_t() {
         if (e == cudaSuccess) e = prepare_nw<16, S, false, false>();
         if (e == cudaSuccess) e = prepare_nw<8, S, true, true>();
         if (e == cudaSuccess) e = prepare_nw<12, S, true, true>();
+        if (e == cudaSuccess) e = prepare_nw<12, S, true, true, true>();
         if (e == cudaSuccess) e = prepare_nw<8, S, false, true>();
         if (e == cudaSuccess) e = prepare_nw<12, S, false, true>();
     }
@@ -1288,6 +1345,27 @@ cudaError_t launch_batch_step(int nw, bool plain, bool wrap, const BatchInstance
                               : (plain ? TSLB_BATCH(12, false, false) : TSLB_BATCH(12, true, false));
 #undef TSLB_BATCH
     return cudaErrorInvalidValue;
+}
+
+cudaError_t tiles_all_tma(const StepParams& p, int storage, bool wrap, int* flag, cudaStream_t s, bool* all) {
+    *all = false;
+    if (p.closure != CL_PROJECTION || (wrap && storage != ST_FP32)) return cudaSuccess;
+    int h = 1;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        switch (storage) {
+            case ST_FP32:
+                e = wrap ? classify_t<float, true>(p, storage, flag, s) : classify_t<float, false>(p, storage, flag, s);
+                break;
+            case ST_FP16: e = classify_t<__half, false>(p, storage, flag, s); break;
+            case ST_BF16: e = classify_t<__nv_bfloat16, false>(p, storage, flag, s); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) *all = h == 0;
+    return e;
 }
 
 cudaError_t prepare_kernels(int storage) {

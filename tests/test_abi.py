@@ -106,7 +106,7 @@ def test_product_code_does_not_use_the_oracle():
 def test_kernel_options_are_checked_before_touching_the_gpu():
     g = tslb.Grid(8, 8, 8)
     for kw in (dict(closure=2), dict(closure=1, block_warps=16), dict(closure=1, scheme=1), dict(plain_stores=2),
-               dict(plain_stores=-1)):
+               dict(plain_stores=-1), dict(per_tile_loads=2), dict(per_tile_loads=-1)):
         o = tslb.tslb_default_options()
         for k, v in kw.items():
             setattr(o, k, v)
