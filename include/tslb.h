@@ -151,11 +151,12 @@ typedef struct {
                                (rows not a multiple of 16 bytes, grids narrower than a tile with
                                periodic x or y faces); 0 = staged TMA stores (default).  Results
                                are the same either way; tslb_autotune tries both. */
-    int32_t per_tile_loads; /* single grids: 1 = the step kernel chooses its load path tile by tile
-                               (TMA box copies, or element-wise loads where a tile's ghost sources
-                               lie outside its boxes) in every block size; 0 = automatic
-                               (default): at tslb_init the library runs the 12-warp kernel's own
-                               tile set-up once per tile, and where every tile loads by TMA, blocks
+    int32_t per_tile_loads; /* 1 = the step kernel chooses its load path tile by tile (TMA box
+                               copies, or element-wise loads where a tile's ghost sources lie
+                               outside its boxes) in every block size; 0 = automatic (default):
+                               the library runs the 12-warp kernel's own tile set-up once per tile
+                               (single grids at tslb_init, batches when they first take 12-warp
+                               blocks), and where every tile (of every grid) loads by TMA, blocks
                                of 12 warps with staged stores run a kernel compiled for that load
                                path alone (fewer registers and instructions in the plane march).
                                Results are the same either way (for comparison and testing). */
@@ -281,11 +282,11 @@ TSLB_API tslb_status tslb_reset_averages(tslb_ctx* ctx);
 TSLB_API tslb_status tslb_autotune(tslb_ctx* ctx, int32_t steps_per_trial, int32_t* block_warps, int32_t* tile_z,
                                    int32_t* plain_stores);
 
-/* The step kernel form the next tslb_step of a single-grid context launches:
- * *block_warps, *tile_z, *plain_stores, and *tma_only = 1 if it is the kernel
- * compiled for TMA tile loads alone (option per_tile_loads), 0 otherwise (any
- * pointer may be NULL).  Encodes the tensor maps of the current block size if
- * no step has yet.  TSLB_ERR_INVALID_ARG for a batch context. */
+/* The step kernel form the next tslb_step launches: *block_warps,
+ * *tile_z (a batch: its first grid's), *plain_stores, and *tma_only = 1 if
+ * it is the kernel compiled for TMA tile loads alone (option per_tile_loads),
+ * 0 otherwise (any pointer may be NULL).  A single grid's tensor maps of the
+ * current block size are encoded here if no step has yet. */
 TSLB_API tslb_status tslb_step_form(tslb_ctx* ctx, int32_t* block_warps, int32_t* tile_z, int32_t* plain_stores,
                                     int32_t* tma_only);
 

@@ -536,7 +536,7 @@ class BatchSimulation:
     together: one persistent launch per time step, graph-replayed."""
 
     def __init__(self, workloads, stream=None, tile_z: int = 0, block_warps: int = 0, graph_steps: int = 0,
-                 plain_stores: bool = False):
+                 plain_stores: bool = False, per_tile_loads: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("BatchSimulation needs a CUDA device")
@@ -554,6 +554,7 @@ class BatchSimulation:
         o.block_warps = int(block_warps)
         o.graph_steps = int(graph_steps)
         o.plain_stores = 1 if plain_stores else 0
+        o.per_tile_loads = 1 if per_tile_loads else 0
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
         self.options = o
         nbytes = tslb_batch_workspace_bytes(self.grids, o)
@@ -584,6 +585,11 @@ class BatchSimulation:
 
     def autotune(self, steps_per_trial: int = 4):
         return tslb_autotune(self.ctx, steps_per_trial)
+
+    def step_form(self):
+        """(block_warps, tile_z of the first grid, plain_stores, tma_only) of
+        the next step's kernel."""
+        return tslb_step_form(self.ctx)
 
     def fields_numpy(self, i: int):
         import torch

@@ -58,6 +58,9 @@ struct tslb_ctx {
     int batch_nw = 8;
     bool batch_plain = false;
     bool batch_wrap = false;  // some instance has the side-box maps of periodic faces
+    int batch_tma12 = -1;     // every tile of every instance loads by TMA in the 12-warp staged-store
+                              // form: 1 / 0, -1 not yet classified
+    bool per_tile_loads = false;  // option per_tile_loads: no one-load-path forms
     float* staging = nullptr;
     double* partials = nullptr;   // step partials; state-sum partials after max_tiles
     int max_tiles = 0;
@@ -435,6 +438,20 @@ tslb_status upload_batch(tslb_ctx* c) {
     }
     c->batch_wrap = false;
     for (const tslb::BatchInstance& b : di) c->batch_wrap = c->batch_wrap || (b.maps[0].wrap && b.maps[1].wrap);
+    if (c->batch_tma12 < 0 && c->batch_nw == 12 && !c->batch_plain && !c->per_tile_loads) {
+        // which batches the kernel compiled for TMA tile loads alone may run (an
+        // instance without side-box maps is classified as the kernel sees it)
+        bool all = true;
+        for (size_t i = 0; i < di.size() && all; ++i) {
+            bool ok = false;
+            if (di[i].maps[0].valid && di[i].maps[1].valid)
+                CK(tslb::tiles_all_tma(di[i].p, c->storage, c->batch_wrap && di[i].maps[0].wrap && di[i].maps[1].wrap,
+                                       c->counters + 3, c->stream, &ok),
+                   "tile classification");
+            all = ok;
+        }
+        c->batch_tma12 = all ? 1 : 0;
+    }
     if ((int)tiles.size() > c->max_tiles) return bad(c, "batch tile list exceeds its workspace");
     c->ntiles = (int)tiles.size();
     CK(cudaMemcpyAsync(c->dinst, di.data(), di.size() * sizeof(di[0]), cudaMemcpyHostToDevice, c->stream),
@@ -462,6 +479,9 @@ cudaError_t single_maps(tslb_ctx* c, int q, tslb::TileMaps** out) {
     return cudaSuccess;
 }
 
+// Whether a batch step launches the kernel compiled for TMA tile loads alone.
+bool batch_tma_only(const tslb_ctx* c) { return c->batch_tma12 == 1 && c->batch_nw == 12 && !c->batch_plain; }
+
 // One time step from parity q (state buf[q], step counter tdev[q]) to q ^ 1.
 cudaError_t launch_one(tslb_ctx* c, int q) {
     if (c->scheme == 1) {
@@ -488,7 +508,8 @@ cudaError_t launch_one(tslb_ctx* c, int q) {
         return tslb::launch_step(I.p, c->storage, I.buf[q], I.buf[q ^ 1], c->tdev + q, c->tdev + (q ^ 1),
                                  c->partials, c->stream, m);
     }
-    return tslb::launch_batch_step(c->batch_nw, c->batch_plain, c->batch_wrap, c->dinst, c->dtiles, c->ntiles, q,
+    return tslb::launch_batch_step(c->batch_nw, c->batch_plain, c->batch_wrap, batch_tma_only(c), c->dinst,
+                                   c->dtiles, c->ntiles, q,
                                    c->tdev + q, c->tdev + (q ^ 1), c->counters, c->partials, c->sms, c->stream);
 }
 
@@ -643,6 +664,7 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
     c->batch = batch;
     c->batch_nw = o.block_warps > 0 ? o.block_warps : 8;
     c->batch_plain = o.plain_stores != 0;
+    c->per_tile_loads = o.per_tile_loads != 0;
     c->check_every = o.check_every > 0 ? o.check_every : 0;
     int gs = o.graph_steps > 0 ? o.graph_steps : 16;
     c->graph_steps = gs >= 2 ? gs & ~1 : 1;
@@ -734,7 +756,7 @@ tslb_status create(tslb_ctx** out, int count, const tslb_grid* grids, tslb_latti
     if (batch) {
         tslb_status s = upload_batch(c);
         if (s != TSLB_OK) return fail(s);
-    } else if (c->scheme == 0 && !o.per_tile_loads) {
+    } else if (c->scheme == 0 && !c->per_tile_loads) {
         // which grids the step kernel compiled for TMA tile loads alone may run
         const StepParams& p = c->inst[0].p;
         const bool periodic = p.face[0] == tslb::BC_PERIODIC || p.face[2] == tslb::BC_PERIODIC;
@@ -1132,8 +1154,14 @@ tslb_status tslb_autotune(tslb_ctx* c, int32_t steps_per_trial, int32_t* block_w
 tslb_status tslb_step_form(tslb_ctx* c, int32_t* block_warps, int32_t* tile_z, int32_t* plain_stores,
                            int32_t* tma_only) {
     if (!c) return TSLB_ERR_INVALID_ARG;
-    if (c->batch) return bad(c, "the step form is reported for single-grid contexts");
     const Instance& I = c->inst[0];
+    if (c->batch) {
+        if (block_warps) *block_warps = c->batch_nw;
+        if (tile_z) *tile_z = I.p.tile_z;
+        if (plain_stores) *plain_stores = c->batch_plain ? 1 : 0;
+        if (tma_only) *tma_only = batch_tma_only(c) ? 1 : 0;
+        return TSLB_OK;
+    }
     bool to = false;
     if (c->scheme == 0 && I.p.closure == tslb::CL_PROJECTION) {
         CK(cudaSetDevice(c->device), "set device");

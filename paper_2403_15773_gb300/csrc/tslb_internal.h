@@ -149,12 +149,14 @@ int max_partials(const StepParams& p, int storage);
 // Batched FP32 step: tiles[k] = (instance, bx, by, bz) over all instances,
 // taken from counters[parity] by one persistent block per SM on `sms` SMs,
 // blocks of `nw` warps (8 or 12), with plain stores if `plain`, in the form
-// for periodic faces if `wrap` (some instance has side-box maps); tile k
-// writes partials[2k..2k+1].
+// for periodic faces if `wrap` (some instance has side-box maps), compiled
+// for TMA tile loads alone if `tma_only` (12 warps, staged stores: every tile
+// of every instance loads by TMA, tiles_all_tma); tile k writes
+// partials[2k..2k+1].
 cudaError_t prepare_batch_kernels();
-cudaError_t launch_batch_step(int nw, bool plain, bool wrap, const BatchInstance* insts, const int4* tiles,
-                              int ntiles, int parity, const long long* t_in, long long* t_out, int* counters,
-                              double* partials, int sms, cudaStream_t s);
+cudaError_t launch_batch_step(int nw, bool plain, bool wrap, bool tma_only, const BatchInstance* insts,
+                              const int4* tiles, int ntiles, int parity, const long long* t_in, long long* t_out,
+                              int* counters, double* partials, int sms, cudaStream_t s);
 
 // The paper's two-sweep design (ablation): collide+push of the moments M into
 // 34 population arrays `pops` (27 f_i - w_i, then 7 g_k), then the moments of

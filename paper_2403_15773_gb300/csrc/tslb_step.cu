@@ -1064,7 +1064,8 @@ __global__ void __launch_bounds__(32 * NW, 1)
 // instance's parameters are staged in shared memory for the tile; its tensor
 // maps are read from the instance table in device memory.  counters[q]
 // serves the steps of parity q; each launch zeroes the other one for the next.
-template <int NW, bool ST, bool WR>
+// TO: every tile of every grid loads by TMA (tile_class_kernel said so).
+template <int NW, bool ST, bool WR, bool TO = false>
 __global__ void __launch_bounds__(32 * NW, 1)
     step_batch_kernel(const BatchInstance* __restrict__ insts, const int4* __restrict__ tiles, int ntiles,
                       int parity, const long long* __restrict__ t_in, long long* __restrict__ t_out,
@@ -1094,16 +1095,18 @@ __global__ void __launch_bounds__(32 * NW, 1)
         // the grid's tensor maps live in device memory, written before the launch
         const TileMaps* maps = &insts[tl.x].maps[parity];
         if (tid == 0) fence_tensormap_acquire(maps);
+        constexpr int MODE = TO ? TILE_TMA : TILE_ANY;
+        float* const o = const_cast<float*>(s_io[1]);
         bool clean;
         if constexpr (Step2Smem<NW, float, ST, WR>::kTmaStore) {
             clean = staged_stores<NW, float, ST, WR>(maps)
-                        ? step_tile<NW, float, ST, WR, true>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y,
-                                                             tl.z, tl.w, partials + 2 * k)
-                        : step_tile<NW, float, ST, WR, false>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y,
-                                                              tl.z, tl.w, partials + 2 * k);
+                        ? step_tile<NW, float, ST, WR, true, MODE>(sP, maps, s_io[0], o, t, tl.y, tl.z, tl.w,
+                                                                   partials + 2 * k)
+                        : step_tile<NW, float, ST, WR, false, MODE>(sP, maps, s_io[0], o, t, tl.y, tl.z, tl.w,
+                                                                    partials + 2 * k);
         } else {
-            clean = step_tile<NW, float, ST, WR, false>(sP, maps, s_io[0], const_cast<float*>(s_io[1]), t, tl.y, tl.z,
-                                                        tl.w, partials + 2 * k);
+            clean = step_tile<NW, float, ST, WR, false, MODE>(sP, maps, s_io[0], o, t, tl.y, tl.z, tl.w,
+                                                              partials + 2 * k);
         }
         if (!clean) break;  // loads that never landed: take no further tile into this shared memory
     }
@@ -1283,11 +1286,11 @@ cudaError_t classify_t(const StepParams& p, int storage, int* flag, cudaStream_t
     return cudaGetLastError();
 }
 
-template <int NW, bool ST, bool WR>
+template <int NW, bool ST, bool WR, bool TO = false>
 cudaError_t launch_batch_nw(const BatchInstance* insts, const int4* tiles, int ntiles, int parity,
                             const long long* t_in, long long* t_out, int* counters, double* partials, int sms,
                             cudaStream_t s) {
-    step_batch_kernel<NW, ST, WR><<<sms, dim3(32, NW, 1), Step2Smem<NW, float, ST, WR>::BYTES, s>>>(
+    step_batch_kernel<NW, ST, WR, TO><<<sms, dim3(32, NW, 1), Step2Smem<NW, float, ST, WR>::BYTES, s>>>(
         insts, tiles, ntiles, parity, t_in, t_out, counters, partials);
     return cudaGetLastError();
 }
@@ -1312,9 +1315,9 @@ cudaError_t prepare_t() {
     return e;
 }
 
-template <int NW, bool ST, bool WR>
+template <int NW, bool ST, bool WR, bool TO = false>
 cudaError_t prepare_batch_nw() {
-    return cudaFuncSetAttribute(step_batch_kernel<NW, ST, WR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(step_batch_kernel<NW, ST, WR, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Step2Smem<NW, float, ST, WR>::BYTES);
 }
 
@@ -1331,14 +1334,21 @@ cudaError_t prepare_batch_kernels() {
     if (e == cudaSuccess) e = prepare_batch_nw<12, true, true>();
     if (e == cudaSuccess) e = prepare_batch_nw<8, false, true>();
     if (e == cudaSuccess) e = prepare_batch_nw<12, false, true>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12, true, false, true>();
+    if (e == cudaSuccess) e = prepare_batch_nw<12, true, true, true>();
     return e;
 }
 
-cudaError_t launch_batch_step(int nw, bool plain, bool wrap, const BatchInstance* insts, const int4* tiles,
-                              int ntiles, int parity, const long long* t_in, long long* t_out, int* counters,
-                              double* partials, int sms, cudaStream_t s) {
+cudaError_t launch_batch_step(int nw, bool plain, bool wrap, bool tma_only, const BatchInstance* insts,
+                              const int4* tiles, int ntiles, int parity, const long long* t_in, long long* t_out,
+                              int* counters, double* partials, int sms, cudaStream_t s) {
 #define TSLB_BATCH(NW_, ST_, WR_) \
     launch_batch_nw<NW_, ST_, WR_>(insts, tiles, ntiles, parity, t_in, t_out, counters, partials, sms, s)
+    if (nw == 12 && !plain && tma_only)
+        return wrap ? launch_batch_nw<12, true, true, true>(insts, tiles, ntiles, parity, t_in, t_out, counters,
+                                                            partials, sms, s)
+                    : launch_batch_nw<12, true, false, true>(insts, tiles, ntiles, parity, t_in, t_out, counters,
+                                                             partials, sms, s);
     if (nw == 8) return wrap ? (plain ? TSLB_BATCH(8, false, true) : TSLB_BATCH(8, true, true))
                              : (plain ? TSLB_BATCH(8, false, false) : TSLB_BATCH(8, true, false));
     if (nw == 12) return wrap ? (plain ? TSLB_BATCH(12, false, true) : TSLB_BATCH(12, true, true))

@@ -160,3 +160,33 @@ def test_full_ensemble_in_the_benchmark_configuration():
         for k in range(4):
             assert np.array_equal(got[k], ref[k]), (i, k)
     b.close()
+
+
+def test_batch_one_load_path_form_equals_per_tile_form():
+    """A batch whose grids all load every tile by TMA (16-byte rows; periodic
+    grids wider than a tile, through the side boxes) runs 12-warp
+    staged-store steps in the kernel compiled for TMA loads alone: the same
+    bits and sums as the per-tile kernel (option per_tile_loads); one narrow
+    periodic grid in the batch (its only tile wraps both ways) keeps the
+    per-tile kernel for the whole batch."""
+    ws = [inputs.droplet_workload(48, radius=11.0),
+          inputs.jet_workload(56, 48, 40, diameter=8, we=300, seed=11, side="periodic"),
+          inputs.jet_workload(72, 50, 30, diameter=10, we=50, seed=12)]
+    runs = []
+    for per_tile in (False, True):
+        b = tslb.BatchSimulation(ws, block_warps=12, tile_z=24, per_tile_loads=per_tile)
+        for i, w in enumerate(ws):
+            b.set_state(i, *w.fields())
+        form = b.step_form()
+        b.step(20)
+        runs.append((form, [b.fields_numpy(i) for i in range(len(ws))], [b.sums(i) for i in range(len(ws))]))
+        b.close()
+    assert runs[0][0] == (12, 24, 0, 1), runs[0][0]
+    assert runs[1][0][3] == 0, runs[1][0]
+    for i in range(len(ws)):
+        for k in range(4):
+            assert np.array_equal(runs[0][1][i][k], runs[1][1][i][k]), (i, k)
+        assert runs[0][2][i] == runs[1][2][i]
+    b = tslb.BatchSimulation(ws + [inputs.droplet_workload(24, radius=6.0)], block_warps=12)
+    assert b.step_form()[3] == 0
+    b.close()
