@@ -344,6 +344,8 @@ def run_gpu(args, ws, storage: str, world: int, dist, tile=None, steps=None):
         tile = {"block_warps": nw, "tile_z": tz, "plain_stores": pl}
         tuned = True
     sims += [make(w) for w in ws[1:]]
+    if not two:  # 1: the step kernel compiled for TMA tile loads alone runs
+        tile["tma_only"] = sims[0].step_form()[3]
     cache.clear()
     for sim in sims:
         sim.step(args.warmup)
@@ -398,6 +400,7 @@ def run_batched(args):
     for i, w in enumerate(ws):
         b.set_state(i, *w.fields())
     shape = b.autotune(3)
+    batch_form = b.step_form()
     b.step(args.warmup)
     b.synchronize()
     st, sp = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -442,7 +445,8 @@ def run_batched(args):
             "sequential_tiles": "each grid in the tile shape the autotuner picks for its edge and faces "
                                 f"({len(tuned)} kinds), one grid after another on one stream",
             "gpu_launches": launches,
-            "autotuned": {"block_warps": shape[0], "tile_z": shape[1], "plain_stores": shape[2]},
+            "autotuned": {"block_warps": shape[0], "tile_z": shape[1], "plain_stores": shape[2],
+                          "tma_only": batch_form[3]},
             "workload": "64 cubic grids, edges uniform in {48, 64, 96, 128}, periodic droplets (R = edge/4) "
                         "and jets (D = 0.15 edge, periodic sides), We log-uniform in [10, 2000], seed 4"}
 
