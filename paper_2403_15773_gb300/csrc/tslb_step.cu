@@ -159,10 +159,13 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 // registers and instructions), for launches whose tiles all load by TMA;
 // TILE_CLASSIFY stops after the set-up and returns whether this tile can load
 // by TMA (tile_class_kernel).  The last two exist for blocks of at most 12
-// warps (no tensor-memory carries).
+// warps (no tensor-memory carries).  UR: copies of the march body the plane
+// loop is unrolled into (4 for the single-grid kernel compiled for TMA
+// loads alone; 2 elsewhere: 4 measured slower with the batch kernel's
+// 64-plane slabs).
 constexpr int TILE_ANY = 0, TILE_TMA = 1, TILE_CLASSIFY = 2;
 
-template <int NW, typename S, bool ST, bool WR, bool TS, int MODE = TILE_ANY>
+template <int NW, typename S, bool ST, bool WR, bool TS, int MODE = TILE_ANY, int UR = 2>
 __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* maps, const S* __restrict__ in,
                                           S* __restrict__ out, const long long t, const int bx, const int by,
                                           const int bz, double* __restrict__ part) {
@@ -647,7 +650,7 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
     }
     // (unrolled by two: the z carries and handoffs then pass between the two
     // copies of the body by register renaming instead of moves)
-#pragma unroll 2
+#pragma unroll UR
     for (int i = z0 - 1; i <= z1 + 1; ++i) {
         if (__syncthreads_or(dead)) break;
         const bool dd = i <= z1;  // plane i is one the tile needs (d) of
@@ -1028,19 +1031,19 @@ __global__ void __launch_bounds__(32 * NW, 1)
     step2_kernel(const __grid_constant__ StepParams P, const __grid_constant__ TileMaps M, const S* __restrict__ in,
                  S* __restrict__ out, const long long* __restrict__ t_in, long long* __restrict__ t_out,
                  double* __restrict__ partials) {
-    constexpr int MODE = TO ? TILE_TMA : TILE_ANY;
+    constexpr int MODE = TO ? TILE_TMA : TILE_ANY, UR = TO ? 4 : 2;
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const long long t = *t_in;
     if constexpr (Step2Smem<NW, S, ST, WR>::kTmaStore) {
         if (staged_stores<NW, S, ST, WR>(&M))
-            step_tile<NW, S, ST, WR, true, MODE>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
-                                                 partials + 2 * blk);
+            step_tile<NW, S, ST, WR, true, MODE, UR>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                     partials + 2 * blk);
         else
-            step_tile<NW, S, ST, WR, false, MODE>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
-                                                  partials + 2 * blk);
+            step_tile<NW, S, ST, WR, false, MODE, UR>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                      partials + 2 * blk);
     } else {
-        step_tile<NW, S, ST, WR, false, MODE>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
-                                              partials + 2 * blk);
+        step_tile<NW, S, ST, WR, false, MODE, UR>(P, &M, in, out, t, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                  partials + 2 * blk);
     }
     if (blk == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_out = t + 1;
 }
