@@ -11,7 +11,8 @@ tile must load element by element (a periodic grid narrower than one tile;
 16-bit storage across periodic faces, which has no side boxes; rows that are
 not a multiple of 16 bytes; 8-warp blocks; plain stores); and after 12 steps
 its stored state and FP64 sums equal, bit for bit, those of the per-tile
-kernel (per_tile_loads = 1).  The oracle parity of the form comes from the
+kernel (per_tile_loads = 1), also for slab depths that leave every
+remainder of the march unrolled by four.  The oracle parity of the form comes from the
 12-warp parity tests, which run it wherever it applies."""
 import pytest
 import torch
@@ -33,6 +34,14 @@ def run(w, storage="fp32", **kw):
     sums = sim.sums()
     sim.close()
     return form, state, sums
+
+
+def close_totals(got, ref):
+    """FP64 totals of the same state summed over other tiles: each thread adds
+    at most 64 planes in FP32 before the FP64 reduction, and that grouping
+    follows the tile shape."""
+    for x, y in zip(got, ref):
+        assert abs(x - y) <= 64 * 2.0 ** -24 * abs(y), (got, ref)
 
 
 def jet72(side="free_slip"):  # 72 columns: 16-byte rows in FP32 and 16 bits; ragged x and y tiles
@@ -72,10 +81,7 @@ def test_other_forms_choose_per_tile(kw):
     fb, b, sb = run(w)
     assert fb[3] == 1, fb
     assert torch.equal(a, b)
-    # the same state; the FP64 totals of 8-warp tiles group the same values
-    # into other partial sums
-    for x, y in zip(sa, sb):
-        assert abs(x - y) <= 1e-9 * abs(y)
+    close_totals(sa, sb)
 
 
 def test_autotuned_12_warp_form_reports_tma_only():
@@ -88,3 +94,18 @@ def test_autotuned_12_warp_form_reports_tma_only():
     assert form[:3] == (nw, tz, pl)
     assert form[3] == (1 if (nw, pl) == (12, 0) else 0), form
     sim.close()
+
+
+@pytest.mark.parametrize("tile_z", [1, 2, 3, 4, 5, 6, 7, 9, 30])
+def test_tma_only_form_independent_of_slab_depth(tile_z):
+    """The TMA-only form unrolls its plane march by four: slab depths whose
+    march (tile_z + 3 planes) leaves every remainder mod 4, and the single
+    slab of the whole grid, give the same bits as the per-tile form in its
+    default slabs."""
+    w = jet72()
+    fa, a, sa = run(w, tile_z=tile_z)
+    assert fa[3] == 1 and fa[1] == tile_z, fa
+    fb, b, sb = run(w, per_tile_loads=True)
+    assert fb[3] == 0, fb
+    assert torch.equal(a, b)
+    close_totals(sa, sb)
