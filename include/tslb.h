@@ -272,7 +272,7 @@ TSLB_API tslb_status tslb_reset_averages(tslb_ctx* ctx);
 /* Tile-shape autotuner: times the step kernel for blocks of 8 and 12 warps
  * (and 14 and 16 for one grid under the projection closure; with FP32 storage under
  * the projection closure also the 8-, 12- and 16-warp forms with plain_stores) and
- * z slabs of 16, 24, 32, 48 and 64 planes, plus, for one grid, the slab
+ * z slabs of 16, 24, 32, 48 and 64 planes (a batch also 128), plus, for one grid, the slab
  * depths whose block count fills 2 to 8 waves of one block per SM to at least
  * 90 % (steps_per_trial launches each, CUDA events on the context stream), and
  * keeps the fastest for all later steps.  Every trial recomputes the step from

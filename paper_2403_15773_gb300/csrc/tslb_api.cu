@@ -1033,6 +1033,7 @@ tslb_status tslb_get_time(const tslb_ctx* c, int64_t* t) {
 // (a last, partly empty wave costs as much as a full one).
 std::vector<int> slab_candidates(const tslb_ctx* c, int nw) {
     std::vector<int> tz(std::begin(kAutotuneTileZ), std::end(kAutotuneTileZ));
+    if (c->batch) tz.push_back(128);  // fewer re-staged planes; a batch's grids still give many tiles
     if (!c->batch) {
         const StepParams& p = c->inst[0].p;
         const long long txy = tiles_of(p, c->storage, nw, p.nz);  // tiles of one full-depth slab
