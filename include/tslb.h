@@ -156,9 +156,10 @@ typedef struct {
                                outside its boxes) in every block size; 0 = automatic (default):
                                the library runs the 12-warp kernel's own tile set-up once per tile
                                (single grids at tslb_init, batches when they first take 12-warp
-                               blocks), and where every tile (of every grid) loads by TMA, blocks
-                               of 12 warps with staged stores run a kernel compiled for that load
-                               path alone (fewer registers and instructions in the plane march).
+                               blocks), and where every tile (of every grid) loads by TMA and the
+                               option average is off, blocks of 12 warps with staged stores run a
+                               kernel compiled for that load path alone (fewer registers and
+                               instructions in the plane march).
                                Results are the same either way (for comparison and testing). */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = a stream the library creates
                                (blocking, so ordered with the legacy default stream) */

@@ -465,7 +465,7 @@ tslb_status upload_batch(tslb_ctx* c) {
 // The tensor maps of a single grid's projection step from parity q, made
 // for the current block size if they were made for another one, with
 // all_tma set where the 12-warp form may run the kernel compiled for TMA
-// tile loads alone.
+// tile loads alone (which keeps no time sums).
 cudaError_t single_maps(tslb_ctx* c, int q, tslb::TileMaps** out) {
     Instance& I = c->inst[0];
     tslb::TileMaps& m = I.maps[q];
@@ -474,13 +474,15 @@ cudaError_t single_maps(tslb_ctx* c, int q, tslb::TileMaps** out) {
         if (e != cudaSuccess) return e;
         m.block_warps = I.p.block_warps;
     }
-    m.all_tma = m.valid && I.p.block_warps == 12 && c->tma12[m.wrap ? 1 : 0] ? 1 : 0;
+    m.all_tma = m.valid && I.p.block_warps == 12 && !c->average && c->tma12[m.wrap ? 1 : 0] ? 1 : 0;
     *out = &m;
     return cudaSuccess;
 }
 
 // Whether a batch step launches the kernel compiled for TMA tile loads alone.
-bool batch_tma_only(const tslb_ctx* c) { return c->batch_tma12 == 1 && c->batch_nw == 12 && !c->batch_plain; }
+bool batch_tma_only(const tslb_ctx* c) {
+    return c->batch_tma12 == 1 && c->batch_nw == 12 && !c->batch_plain && !c->average;
+}
 
 // One time step from parity q (state buf[q], step counter tdev[q]) to q ^ 1.
 cudaError_t launch_one(tslb_ctx* c, int q) {

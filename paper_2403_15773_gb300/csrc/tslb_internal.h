@@ -74,8 +74,9 @@ struct TileMaps {
     int store;
     int wrap;
     int block_warps;
-    int all_tma;  // every tile of the grid loads by TMA (tiles_all_tma): 12-warp blocks with
-                  // staged stores run the step kernel compiled for that load path alone
+    int all_tma;  // every tile of the grid loads by TMA (tiles_all_tma) and no time sums are
+                  // kept: 12-warp blocks with staged stores run the step kernel compiled for
+                  // that load path alone
 };
 
 

@@ -156,7 +156,8 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 // the march has no branch on it.
 // MODE: TILE_ANY chooses the load path per tile at run time; TILE_TMA is
 // compiled for TMA loads alone (no element-wise path in the march: fewer
-// registers and instructions), for launches whose tiles all load by TMA;
+// registers and instructions) and without the time sums of phi and u_z, for
+// launches whose tiles all load by TMA and that keep no time sums;
 // TILE_CLASSIFY stops after the set-up and returns whether this tile can load
 // by TMA (tile_class_kernel).  The last two exist for blocks of at most 12
 // warps (no tensor-memory carries).  UR: copies of the march body the plane
@@ -938,7 +939,9 @@ __device__ __forceinline__ bool step_tile(const StepParams& P, const TileMaps* m
             for (int k = 0; k < 6; ++k) tmem_st8(tm_addr + 64u + 8u * k, c + 8 * k);
             tmem_wait_st48(c);
         }
-        if (P.avg && (outA || outB)) {  // time sums of the new phi and u_z of plane i - 2 (FP64)
+        // time sums of the new phi and u_z of plane i - 2 (FP64; TILE_TMA is
+        // launched only without them)
+        if (MODE != TILE_TMA && P.avg && (outA || outB)) {
             const long long zo = nxy * (i - 2);
             if (outA) {
                 double* a = P.avg + zo + sxyA;

@@ -109,3 +109,16 @@ def test_tma_only_form_independent_of_slab_depth(tile_z):
     assert fb[3] == 0, fb
     assert torch.equal(a, b)
     close_totals(sa, sb)
+
+
+def test_time_sums_keep_the_per_tile_form():
+    """The TMA-only form keeps no time sums of phi and u_z: with the option
+    average on, the same grid runs the per-tile form (whose averages the
+    parity tests check against the oracle)."""
+    w = jet72()
+    fa, a, sa = run(w, average=True)
+    assert fa[0] == 12 and fa[3] == 0, fa
+    fb, b, sb = run(w)
+    assert fb[3] == 1, fb
+    assert torch.equal(a, b)
+    assert sa == sb
